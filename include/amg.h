@@ -1,0 +1,211 @@
+/*
+ * amg.h - C ABI of the GB300 library for the solve phase of the
+ * single-hierarchy multiple-vector aggregation-based AMG (D'Ambra &
+ * Vassilevski, "Improving Solve Time of Aggregation-based Adaptive AMG"),
+ * used as a preconditioner for conjugate gradients.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Plain C types only.  Pointers may address device memory or host memory
+ *    (pageable or pinned); the library inspects each pointer and stages host
+ *    buffers through its own device buffers.  Index arrays are int32.
+ *  - Multi-column vectors are dense row-major n x nrhs blocks (the nrhs
+ *    values of one row are contiguous).
+ *  - ``stream`` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Work is ordered after earlier work on that stream.
+ *    Every call returns only after its results are final (it synchronises
+ *    once at the end), so status codes and info structs are valid on return.
+ *  - No exception or CUDA error crosses the ABI: every call returns an
+ *    amg_status and leaves a message for amg_last_error().  Invalid
+ *    arguments are rejected before any launch.
+ *  - Handles are not thread-safe: one handle must not be used by two host
+ *    threads at the same time.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amg_hierarchy* amg_handle;   /* opaque, owned by the library */
+
+typedef enum {
+  AMG_OK = 0,
+  AMG_ERR_INVALID_ARG = 1,   /* malformed CSR, aggregate map, size or option        */
+  AMG_ERR_NOT_SPD = 2,       /* non-positive pivot in the coarsest Cholesky          */
+  AMG_ERR_NOT_CONVERGED = 3, /* maxit reached; x and info are still written          */
+  AMG_ERR_BREAKDOWN = 4,     /* p.q <= 0 or a non-finite CG scalar; x is written     */
+  AMG_ERR_TIMEOUT = 5,       /* a bounded device wait gave up                         */
+  AMG_ERR_CUDA = 6,          /* a CUDA runtime call failed                            */
+  AMG_ERR_ALLOC = 7          /* device or host allocation failed                      */
+} amg_status;
+
+/* Square sparse matrix in CSR form: rowptr[n+1], col[nnz] (sorted, in
+ * range), val[nnz] (float64).  The library copies it during setup and never
+ * aliases it afterwards. */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+} amg_csr;
+
+typedef struct {
+  double tol_svd;          /* TOL of the truncation rule (Section 5): keep the left
+                              singular vectors with sigma > TOL*size(a)/size(A). 0.1 */
+  int32_t pre;             /* l1-Jacobi pre-sweeps per level (>= 1).              1 */
+  int32_t post;            /* l1-Jacobi post-sweeps per level (>= 1).             1 */
+  int32_t cycle_precision; /* 64: whole V-cycle in float64; 32: V-cycle in float32
+                              inside float64 CG (coarsest solve stays float64).  64 */
+  double rtol;             /* stop when ||r||_2 <= rtol*||b||_2 (recursive r). 1e-8 */
+  int32_t maxit;           /* iteration limit.                                 1000 */
+  int32_t use_graph;       /* 1: PCG iterations replayed from a CUDA graph.      1 */
+  int32_t check_every;     /* iterations between convergence reads on the host.  8 */
+  int32_t autotune;        /* 1: time SpMV lane layouts once per (level, nrhs).  1 */
+} amg_opts;
+
+/* Per right-hand-side result. */
+typedef struct {
+  int32_t iters;       /* PCG iterations performed                               */
+  int32_t converged;   /* 1 if ||r|| <= rtol ||b||                                */
+  int32_t status;      /* amg_status of this column                              */
+  int32_t reserved;
+  double relres;       /* final recursive relative residual ||r||/||b||          */
+} amg_info;
+
+/* Hierarchy characteristics (Section 5: nl, opc, cr). */
+typedef struct {
+  int32_t levels;          /* nl, including the fine level                       */
+  int32_t m;               /* number of smooth vectors                           */
+  double opc;              /* sum_k nnz(A^k) / nnz(A^0)                          */
+  double cr;               /* mean of n(A^{k-1})/n(A^k) over the nl-1 steps      */
+  int64_t n_level[16];
+  int64_t nnz_level[16];
+  int64_t truncated_aggs;  /* aggregates that kept fewer than min(n_a, m) columns */
+  int64_t device_bytes;    /* device memory held by the hierarchy                */
+} amg_hier_info;
+
+/* Fill *opts with the defaults listed above. */
+void amg_default_opts(amg_opts* opts);
+
+/*
+ * Build the multiple-vector hierarchy (Section 4, Eq. (svd); Section 4.1).
+ *
+ *  A           fine matrix, SPD (host or device arrays).
+ *  n_agg_levels L-1: number of aggregate maps, 0 <= L-1 <= 15.
+ *  agg[k]      int32[n_nodes[k]]: level-(k+1) aggregate of level-k node i
+ *              (the binary matrices pi^{k+1} of Eq. (binmat)).  Level-0 nodes
+ *              are the dofs; level-k nodes (k >= 1) are the level-k aggregates,
+ *              each owning the coarse dofs its local basis produced (the matrix
+ *              Q of Section 4.1).  Every aggregate must be non-empty.
+ *  n_nodes     int32[L] host array: n_nodes[0] = A->n, n_nodes[k] = number of
+ *              level-k aggregates.
+ *  W           float64 n x m column-major: the smooth vectors w_0..w_{m-1}.
+ *  m           1 <= m <= 16.
+ *
+ * For each level: local SVD of W|_a per aggregate, truncation with
+ * opts->tol_svd, block prolongator P^k = blockdiag(P~_a) with orthonormal
+ * columns, Galerkin A^k = (P^k)^T A^{k-1} P^k, coarse smooth vectors
+ * (P^k)^T W^{k-1}; all on the device.  The coarsest matrix is factorised by a
+ * float64 Cholesky on the device (AMG_ERR_NOT_SPD on a non-positive pivot).
+ * On success *out owns all device memory of the hierarchy until amg_destroy.
+ */
+amg_status amg_setup_from_aggregates(const amg_csr* A, int32_t n_agg_levels,
+                                     const int32_t* const* agg, const int32_t* n_nodes,
+                                     const double* W, int32_t m, const amg_opts* opts,
+                                     void* stream, amg_handle* out);
+
+/*
+ * AMG-preconditioned CG (Section 5) for nrhs right-hand sides at once.
+ *  b  n x nrhs row-major float64 (host or device), read only.
+ *  x  n x nrhs row-major float64 (host or device): initial guess on entry,
+ *     solution on return (also on NOT_CONVERGED / BREAKDOWN).
+ *  info  host array of nrhs amg_info, or NULL.
+ * Each column runs its own CG (own alpha, beta, stopping test); the matrix
+ * and the hierarchy are read once per sweep for all columns.
+ */
+amg_status amg_solve(amg_handle h, const double* b, double* x, int32_t nrhs,
+                     const amg_opts* opts, void* stream, amg_info* info);
+
+/*
+ * Solve nsys independent systems (each with its own hierarchy and nrhs[s]
+ * right-hand sides) in one launch sequence: the hierarchies are concatenated
+ * block-diagonally level by level, the coarsest solve is block-diagonal and
+ * the CG scalars are kept per (system, column).  All hierarchies must have the
+ * same number of levels.  b[s], x[s] are n_s x nrhs[s] row-major (host or
+ * device); info is a host array of sum(nrhs) entries, system-major, or NULL.
+ * The concatenated hierarchy is built on the first call for a given list of
+ * handles and cached on h[0] until amg_destroy(h[0]).
+ */
+amg_status amg_solve_batched(const amg_handle* h, int32_t nsys, const double* const* b,
+                             double* const* x, const int32_t* nrhs, const amg_opts* opts,
+                             void* stream, amg_info* info);
+
+/*
+ * Adjoint of x = A^{-1} b (A SPD, so A^{-T} = A^{-1}): solves A lambda = g
+ * with the same preconditioned CG and writes, for every stored entry (i, j) of
+ * the setup matrix A in its CSR order,
+ *     grad_val[p] = - sum_c lambda[i, c] * x[j, c],
+ * the derivative of L with respect to a_ij when g = dL/dx.
+ *  g, x     n x nrhs row-major float64 (host or device).
+ *  lambda   n x nrhs row-major float64 output (host or device); zero initial guess.
+ *  grad_val nnz float64 output (host or device).
+ */
+amg_status amg_adjoint(amg_handle h, const double* g, const double* x, int32_t nrhs,
+                       double* lambda, double* grad_val, const amg_opts* opts,
+                       void* stream, amg_info* info);
+
+/* Apply the preconditioner once, z = B r (one V-cycle, Section 5), in the
+ * precision opts->cycle_precision.  r, z: n x nrhs row-major float64. */
+amg_status amg_vcycle(amg_handle h, const double* r, double* z, int32_t nrhs,
+                      const amg_opts* opts, void* stream);
+
+/* Hierarchy characteristics; never fails for a valid handle. */
+amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info);
+
+/*
+ * Export level k of the hierarchy to host arrays, for inspection and tests.
+ * sizes (int64[6], always filled): n_k, nnz_k, number of level-k aggregates
+ * (0 for k = 0), number of prolongator values, n_{k-1} (0 for k = 0), m.
+ * Any output pointer may be NULL.  The library numbers dofs internally in an
+ * order where every aggregate is contiguous; the export describes it:
+ *   rowptr[n_k+1], col[nnz_k], val[nnz_k]  A^k in the library's numbering;
+ *   perm[n_k]     for k = 0: library dof -> caller dof;
+ *   agg_id[naggs] library aggregate -> caller aggregate index (level k);
+ *   r[naggs]      kept columns per aggregate;
+ *   row_start[naggs+1] level-(k-1) rows of each aggregate (library numbering);
+ *   pval          prolongator blocks, aggregate after aggregate, each n_a x r_a
+ *                 row-major (float64).
+ */
+amg_status amg_export_level(amg_handle h, int32_t k, int64_t* sizes, int32_t* rowptr,
+                            int32_t* col, double* val, int32_t* perm, int32_t* agg_id,
+                            int32_t* r, int32_t* row_start, double* pval);
+
+/* Kernel timing hook used by the benchmark: while enabled, every launch of
+ * the kernel family ``kernel_id`` (AMG_KERNEL_*) is bracketed by CUDA events
+ * on the stream it is launched on; amg_timer_read returns the summed device
+ * time and the number of launches since the last enable. */
+enum {
+  AMG_KERNEL_SPMV_CG = 1,        /* q = A p with p.q            (level 0, float64) */
+  AMG_KERNEL_RESTRICT_L0 = 2,    /* fused residual + P^T        (level 0)          */
+  AMG_KERNEL_SMOOTH_L0 = 3,      /* post-smoothing with r.z     (level 0)          */
+  AMG_KERNEL_PROLONG_L0 = 4,     /* x += P e                    (level 0)          */
+  AMG_KERNEL_CG_UPDATE = 5       /* x, r update with ||r||      (level 0)          */
+};
+amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
+amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);
+
+void amg_destroy(amg_handle h);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_H */

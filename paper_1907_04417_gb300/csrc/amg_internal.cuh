@@ -1,0 +1,201 @@
+// Internal declarations of the GB300 AMG library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+
+namespace amg {
+
+// ---------------------------------------------------------------- errors --
+struct Error : std::runtime_error {
+  amg_status status;
+  Error(amg_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define AMG_CUDA(call)                                                             \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      throw ::amg::Error(AMG_ERR_CUDA, std::string(#call " failed: ") +            \
+                                           cudaGetErrorString(e_) + " at " +       \
+                                           __FILE__ + ":" + std::to_string(__LINE__)); \
+  } while (0)
+
+#define AMG_REQUIRE(cond, msg)                                                     \
+  do {                                                                             \
+    if (!(cond)) throw ::amg::Error(AMG_ERR_INVALID_ARG, msg);                     \
+  } while (0)
+
+#define AMG_LAUNCH_CHECK() AMG_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------- memory --
+// All device memory of a hierarchy (and of its solve workspaces) is taken
+// from an arena that frees everything at destruction.
+struct Arena {
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  void* raw(size_t n) {
+    if (n == 0) n = 16;
+    n = (n + 255) & ~size_t(255);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(AMG_ERR_ALLOC, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+    }
+    blocks.push_back(p);
+    bytes += n;
+    return p;
+  }
+  template <typename T> T* alloc(size_t count) { return static_cast<T*>(raw(count * sizeof(T))); }
+  ~Arena() {
+    for (void* p : blocks) cudaFree(p);
+  }
+};
+
+// ------------------------------------------------------------ hierarchy --
+// Every level is numbered so that each aggregate of the next level owns a
+// contiguous range of rows; the prolongator of an aggregate is then a dense
+// n_a x r_a block applied to a contiguous slice.
+struct Level {
+  int n = 0;
+  long long nnz = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* val64 = nullptr;
+  float* val32 = nullptr;
+  double* dinv64 = nullptr;  // 1 / sum_j |a_ij|   (non-coarsest levels)
+  float* dinv32 = nullptr;
+  // contiguous row ranges, one per CTA, for the row-parallel kernels
+  int ncta = 0;
+  int* cta_row = nullptr;
+  std::vector<int> h_cta_row;
+  int max_row_len = 0;
+  double avg_row_len = 0;
+};
+
+// P^{k+1}: maps level k+1 (coarse) to level k (fine).
+struct Transfer {
+  int nagg = 0, nf = 0, nc = 0;
+  long long npval = 0;
+  int* row_start = nullptr;        // nagg + 1, fine rows of each aggregate
+  int* coarse_start = nullptr;     // nagg + 1, coarse dofs of each aggregate
+  long long* blk_start = nullptr;  // nagg + 1, offsets of the n_a x r_a blocks
+  double* p64 = nullptr;
+  float* p32 = nullptr;
+  int ncta = 0;                    // aggregate-aligned CTA ranges
+  int* cta_agg = nullptr;
+  int max_rows_cta = 0;
+  std::vector<int> h_row_start, h_coarse_start;
+  std::vector<long long> h_blk_start;
+};
+
+// Dense inverses of the coarsest matrix (block-diagonal over systems).
+struct Coarsest {
+  int n = 0, nblk = 0;
+  int* blk_off = nullptr;          // nblk + 1 rows
+  long long* inv_off = nullptr;    // nblk + 1 offsets into inv
+  double* inv = nullptr;
+  std::vector<int> h_blk_off;
+  std::vector<long long> h_inv_off;
+};
+
+// Device-side CG scalars, one entry per (system, column).
+struct CGState {
+  double* rho;
+  double* alpha;
+  double* beta;
+  double* bnorm;
+  double* rnorm;
+  int* conv;
+  int* iters;
+  int* status;
+  int* active_cols;  // per system: number of real columns (nrhs_s)
+  int* done;         // set when every real column stopped
+  int* iter;         // global iteration counter
+  unsigned* counters;
+  double rtol;
+  int maxit;
+};
+
+struct Workspace;
+
+struct Plan {
+  int L = 0, nsys = 1, m = 0;
+  std::vector<Level> lev;
+  std::vector<Transfer> tr;   // tr[k] maps level k+1 -> level k
+  Coarsest co;
+  std::vector<int> h_sys_row;  // nsys + 1 level-0 row offsets
+  std::vector<int> h_sys_cta;  // nsys + 1 level-0 CTA offsets
+  int* sys_cta = nullptr;
+  int* perm0 = nullptr;        // library row -> row within its own system (caller numbering)
+  std::unique_ptr<Arena> arena;
+  std::map<long long, std::shared_ptr<Workspace>> ws;
+  Plan() : arena(new Arena) {}
+  ~Plan();
+};
+
+struct Timer {
+  int kernel = 0;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // pairs
+  size_t used = 0;
+  double total_ms = 0;
+  long long launches = 0;
+};
+
+}  // namespace amg
+
+struct amg_hierarchy {
+  amg::Plan plan;
+  int n = 0, nnz = 0, m = 0;
+  int* nzmap = nullptr;                   // library nz -> caller nz (level 0)
+  std::vector<std::vector<int>> h_perm;   // per level: library node -> caller node
+  std::vector<std::vector<int>> h_r;      // per coarse level: kept columns per aggregate
+  long long truncated = 0;
+  amg::Timer timer;
+  cudaStream_t own = nullptr;            // internal non-blocking stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::map<std::vector<amg_hierarchy*>, std::unique_ptr<amg::Plan>> batches;
+};
+
+namespace amg {
+
+// setup (amg_setup.cu)
+void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t* const* agg,
+                     const int32_t* n_nodes, const double* W, int m, const amg_opts& o,
+                     cudaStream_t st);
+void build_batch_plan(Plan& out, const std::vector<amg_hierarchy*>& hs, cudaStream_t st);
+void make_row_partition(Plan& P, int k, int target_rows, const std::vector<int>& sys_rows,
+                        cudaStream_t st);
+
+// solve (amg_solve.cu)
+struct SolveReq {
+  int nsys;
+  std::vector<int> n_sys;
+  std::vector<const double*> b;
+  std::vector<double*> x;
+  std::vector<int> nrhs;
+  bool zero_x;  // ignore the contents of x (adjoint)
+};
+amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_opts& o,
+                   cudaStream_t user, amg_info* info);
+void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int nrhs,
+                const amg_opts& o, cudaStream_t user);
+void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* x_caller,
+                      int nrhs, double* grad, cudaStream_t st);
+
+// pointer helpers
+bool is_device_ptr(const void* p);
+void copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
+void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st);
+
+}  // namespace amg

@@ -1,0 +1,204 @@
+// Host-side launchers of the V-cycle kernels, templated on the cycle
+// precision TC.  Each precision is instantiated in its own translation unit
+// (amg_cycle_f64.cu, amg_cycle_f32.cu) so that they compile in parallel.
+#pragma once
+
+#include <type_traits>
+
+#include "amg_kernels.cuh"
+
+namespace amg {
+
+template <int V>
+using ic = std::integral_constant<int, V>;
+
+template <class F>
+inline void dispatch_k(int K, F&& f) {
+  switch (K) {
+    case 1: f(ic<1>{}); break;
+    case 2: f(ic<2>{}); break;
+    case 4: f(ic<4>{}); break;
+    case 8: f(ic<8>{}); break;
+    case 16: f(ic<16>{}); break;
+    case 32: f(ic<32>{}); break;
+    default: throw Error(AMG_ERR_INVALID_ARG, "internal: unsupported column count " + std::to_string(K));
+  }
+}
+
+// Lanes per row along the non-zeros: {2..32} for one column, {1..8} otherwise.
+template <class F>
+inline void dispatch_nzl(int K, int nzl, F&& f) {
+  if (K == 1) {
+    switch (nzl) {
+      case 2: f(ic<2>{}); return;
+      case 4: f(ic<4>{}); return;
+      case 8: f(ic<8>{}); return;
+      case 16: f(ic<16>{}); return;
+      case 32: f(ic<32>{}); return;
+    }
+  } else {
+    switch (nzl) {
+      case 1: f(ic<1>{}); return;
+      case 2: f(ic<2>{}); return;
+      case 4: f(ic<4>{}); return;
+      case 8: f(ic<8>{}); return;
+    }
+  }
+  throw Error(AMG_ERR_INVALID_ARG, "internal: unsupported lane layout");
+}
+
+template <typename TC>
+inline int max_nzl(int K) {
+  int cpt = (K * (int)sizeof(TC) >= 16) ? 16 / (int)sizeof(TC) : K;
+  int cl = K / cpt;
+  int m = 32 / cl;
+  if (K == 1) return 32;
+  return m < 8 ? m : 8;
+}
+
+template <typename TC>
+inline const TC* vals(const Level& L) {
+  if constexpr (std::is_same<TC, double>::value) return L.val64; else return L.val32;
+}
+template <typename TC>
+inline const TC* dinvs(const Level& L) {
+  if constexpr (std::is_same<TC, double>::value) return L.dinv64; else return L.dinv32;
+}
+template <typename TC>
+inline const TC* pvals(const Transfer& T) {
+  if constexpr (std::is_same<TC, double>::value) return T.p64; else return T.p32;
+}
+
+// Raise the dynamic shared-memory limit of a kernel once (and never while a
+// stream is being captured: the first call of every launcher happens in the
+// eager start-up sequence of a solve).
+template <typename Kern>
+inline void ensure_smem(Kern k, size_t bytes) {
+  static std::map<const void*, size_t> granted;
+  const void* key = reinterpret_cast<const void*>(k);
+  auto it = granted.find(key);
+  size_t have = it == granted.end() ? 48 * 1024 : it->second;
+  if (bytes > have) {
+    AMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    granted[key] = bytes;
+  }
+}
+
+template <typename TC>
+void launch_smooth(int K, int nzl, const Level& L, const TC* f, const TC* u, TC* v, const int* done,
+                   cudaStream_t st);
+template <typename TC>
+void launch_restrict(int K, int nzl, const Level& L, const Transfer& T, const Level& C, bool smooth_next,
+                     const TC* f, const TC* u, TC* fc, TC* uc, const int* done, cudaStream_t st);
+template <typename TC>
+void launch_prolong(int K, const Transfer& T, const TC* uc, TC* u, const int* done, cudaStream_t st);
+template <typename TC>
+void launch_coarse(int K, const Coarsest& C, const TC* f, TC* u, const int* done, cudaStream_t st);
+template <typename TC>
+void launch_post0(int K, int nzl, const Level& L, const TC* f, const TC* u, const double* r, double* z,
+                  const KState& ks, int mode, cudaStream_t st);
+template <typename TC>
+void launch_update(int K, const Level& L, double* x, double* r, const double* p, const double* q, TC* u0,
+                   TC* f0, const KState& ks, cudaStream_t st);
+template <typename TC>
+void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, const int* done,
+                       cudaStream_t st);
+
+#define AMG_DEFINE_LAUNCHERS(TC)                                                                       \
+  template <>                                                                                          \
+  void launch_smooth<TC>(int K, int nzl, const Level& L, const TC* f, const TC* u, TC* v,              \
+                         const int* done, cudaStream_t st) {                                           \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
+        constexpr int NZ = decltype(nc)::value;                                                        \
+        if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
+          k_smooth<TC, KK, NZ><<<L.ncta, BS, 0, st>>>(L.cta_row, L.rowptr, L.col, vals<TC>(L),        \
+                                                      dinvs<TC>(L), f, u, v, done);                    \
+        } else {                                                                                       \
+          throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
+        }                                                                                              \
+      });                                                                                              \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_restrict<TC>(int K, int nzl, const Level& L, const Transfer& T, const Level& C,          \
+                           bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc,                 \
+                           const int* done, cudaStream_t st) {                                         \
+    size_t smem = (size_t)T.max_rows_cta * K * sizeof(TC);                                             \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
+        constexpr int NZ = decltype(nc)::value;                                                        \
+        if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
+          auto kern = k_restrict<TC, KK, NZ>;                                                          \
+          ensure_smem(kern, smem);                                                                     \
+          kern<<<T.ncta, BS, smem, st>>>(T.cta_agg, T.row_start, T.coarse_start, T.blk_start,          \
+                                         pvals<TC>(T), L.rowptr, L.col, vals<TC>(L), f, u, fc,         \
+                                         smooth_next ? uc : nullptr,                                   \
+                                         smooth_next ? dinvs<TC>(C) : nullptr, done);                  \
+        } else {                                                                                       \
+          throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
+        }                                                                                              \
+      });                                                                                              \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_prolong<TC>(int K, const Transfer& T, const TC* uc, TC* u, const int* done,              \
+                          cudaStream_t st) {                                                           \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      k_prolong<TC, KK><<<T.ncta, BS, 0, st>>>(T.cta_agg, T.row_start, T.coarse_start, T.blk_start,   \
+                                               pvals<TC>(T), uc, u, done);                             \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_coarse<TC>(int K, const Coarsest& C, const TC* f, TC* u, const int* done,                \
+                         cudaStream_t st) {                                                            \
+    int grid = (C.n * 32 + BS - 1) / BS;                                                               \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      k_coarse<TC, KK><<<grid, BS, 0, st>>>(C.n, C.nblk, C.blk_off, C.inv_off, C.inv, f, u, done);    \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_post0<TC>(int K, int nzl, const Level& L, const TC* f, const TC* u, const double* r,     \
+                        double* z, const KState& ks, int mode, cudaStream_t st) {                      \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
+        constexpr int NZ = decltype(nc)::value;                                                        \
+        if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
+          k_post0<TC, KK, NZ><<<L.ncta, BS, 0, st>>>(L.cta_row, L.rowptr, L.col, vals<TC>(L),         \
+                                                     dinvs<TC>(L), f, u, r, z, ks, mode);              \
+        } else {                                                                                       \
+          throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
+        }                                                                                              \
+      });                                                                                              \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_update<TC>(int K, const Level& L, double* x, double* r, const double* p,                 \
+                         const double* q, TC* u0, TC* f0, const KState& ks, cudaStream_t st) {         \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      k_cg_update<TC, KK><<<L.ncta, BS, 0, st>>>(L.cta_row, x, r, p, q, L.dinv64, u0, f0, ks);        \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_presmooth0<TC>(int K, const Level& L, const double* r, TC* u0, TC* f0,                   \
+                             const int* done, cudaStream_t st) {                                       \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      k_presmooth0<TC, KK><<<L.ncta, BS, 0, st>>>(L.cta_row, r, L.dinv64, u0, f0, done);              \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }
+
+}  // namespace amg

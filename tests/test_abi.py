@@ -1,0 +1,47 @@
+"""The C-ABI library builds, loads and exports every symbol include/amg.h
+declares; the binding declares the same set.  No compute call (no GPU here)."""
+import os
+import re
+
+import pytest
+
+from paper_1907_04417_gb300 import amg, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "amg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(amg_[a-z_]+)\s*\(", src))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return amg.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"amg_setup_from_aggregates", "amg_solve", "amg_solve_batched", "amg_adjoint"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names == set(amg.SIGNATURES), names ^ set(amg.SIGNATURES)
+
+
+def test_default_options_and_struct_layout(lib):
+    o = amg.opts()
+    assert o.tol_svd == 0.1 and o.pre == 1 and o.post == 1 and o.cycle_precision == 64
+    assert o.rtol == 1e-8 and o.maxit == 1000
+    assert amg.amg_opts.rtol.offset == 24 and amg.amg_info.relres.offset == 16
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    import ctypes
+    assert lib.amg_solve(None, None, None, 1, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "non-null" in amg.last_error()
+    assert lib.amg_setup_from_aggregates(None, 0, None, None, None, 1, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert lib.amg_hierarchy_info(None, None) == amg.AMG_ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    assert lib.amg_setup_from_aggregates(None, 0, None, None, None, 1, None, None, ctypes.byref(out)) != amg.AMG_OK
