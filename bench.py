@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Time to a 1e-8 relative residual per right-hand side for the AMG-PCG
+solve of the rotated anisotropic diffusion problem (eps = 1e-3, theta =
+pi/6, 9-point, 1024 x 1024, 4 smooth vectors, aggregates of 16, 5 levels).
+
+One step = one complete batched solve (float32 V-cycle inside float64 CG)
+of ``--batch`` seeded uniform[-1, 1] right-hand sides from a zero initial
+guess, with inputs resident in HBM.  The plain float64 solve of one RHS is
+timed beside it.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N --steps K --warmup W --impl gb300|reference]
+
+Under torchrun every rank runs an independent replica on its own GPU with
+its own right-hand sides (weak scaling, no collective on the data path); the
+timed region is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms to 1e-8 rel. residual per RHS (FP32-cycle batched AMG-PCG)"
+UNIT = "ms/RHS"
+WORKLOAD = "aniso9 eps=1e-3 theta=pi/6, 1024x1024 (n=1048576), m=4, aggregates of 16, 5 levels"
+PEAK_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--grid", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--maxit", type=int, default=5000)
+    ap.add_argument("--roofline-kernel", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="also time every kernel family once (eager launches)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ dist --
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers --
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return PEAK_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1907_04417_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(ROOT, "paper_1907_04417_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel, workload_key):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(f"{kernel}|{workload_key}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["bytes_per_launch"])
+
+
+def algorithmic_bytes(kernel, lv, K, wc):
+    """Minimal bytes one launch of a level-0 kernel must move (see the
+    roofline section of the design notes): matrix arrays once, each vector
+    block once per read or write, prolongator blocks once."""
+    n0, nnz0, n1, npv = lv["n0"], lv["nnz0"], lv["n1"], lv["npv1"]
+    if kernel == "spmv_cg":      # q = A p (float64), p.q
+        return nnz0 * 12 + 4 * (n0 + 1) + 2 * n0 * K * 8
+    if kernel == "restrict_l0":  # t = f - A u, fc = P^T t, uc = D^-1 fc
+        return nnz0 * (wc + 4) + 4 * (n0 + 1) + 2 * n0 * K * wc + npv * wc + n1 * (2 * K * wc + wc)
+    if kernel == "smooth_l0":    # z = u + D^-1 (f - A u), r.z
+        return nnz0 * (wc + 4) + 4 * (n0 + 1) + n0 * wc + 2 * n0 * K * wc + 2 * n0 * K * 8
+    if kernel == "prolong_l0":   # u += P uc
+        return npv * wc + n1 * K * wc + 2 * n0 * K * wc
+    if kernel == "cg_update":    # x += a p, r -= a q, ||r||, u0 = D^-1 r, f0 = r
+        return 6 * n0 * K * 8 + n0 * 8 + (2 if wc == 4 else 1) * n0 * K * wc
+    raise KeyError(kernel)
+
+
+KERNEL_IDS = {"spmv_cg": 1, "restrict_l0": 2, "smooth_l0": 3, "prolong_l0": 4, "cg_update": 5}
+
+
+# ------------------------------------------------------------ CPU legs --
+def oracle_sample(P, iters_needed, budget_s):
+    """Time the oracle's PCG iterations on the same workload (setup not
+    timed) for about ``budget_s`` seconds; scale to ``iters_needed``."""
+    from oracle import amg_oracle as O
+    H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
+    b = P.B[:, 0]
+    t0 = time.perf_counter()
+    r1 = O.pcg(P.A, b, lambda r: O.vcycle(H, r), fixed_iters=1)
+    t1 = time.perf_counter() - t0
+    k = max(2, int(budget_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    O.pcg(P.A, b, lambda r: O.vcycle(H, r), fixed_iters=k)
+    dt = time.perf_counter() - t0
+    per_it = dt / k
+    return {"per_iter_s": per_it, "sample_iters": k, "sample_s": dt,
+            "ms_per_rhs": per_it * iters_needed * 1e3, "_first": r1.iters}
+
+
+def stored_oracle_iters(N):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    if os.path.exists(p):
+        d = json.load(open(p)).get(f"aniso9_{N}x{N}")
+        if d:
+            return int(d["iters"])
+    return None
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1907_04417_gb300.hostsetup import inputs
+    P = inputs.anisotropic(N=args.grid, nrhs=1)
+    iters = stored_oracle_iters(args.grid)
+    from oracle import amg_oracle as O
+    H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
+    b = P.B[:, 0]
+    k = 3
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.pcg(P.A, b, lambda r: O.vcycle(H, r), fixed_iters=k)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt / k)
+    per_it = statistics.median(times)
+    if iters is None:
+        res = O.pcg(P.A, b, lambda r: O.vcycle(H, r), maxit=args.maxit)
+        iters = res.iters
+    val = per_it * iters * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * k * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "rhs_per_step": 1},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{k} FP64 oracle PCG iterations per step on the same workload "
+                                       f"(setup untimed), scaled to the oracle's {iters} iterations"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- main --
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1907_04417_gb300 import amg, build
+    from paper_1907_04417_gb300.hostsetup import inputs
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_gen = time.time()
+    P = inputs.anisotropic(N=args.grid, nrhs=1)
+    rng = np.random.Generator(np.random.PCG64(1002 + 7919 * rank))
+    B = rng.uniform(-1.0, 1.0, size=(P.n, args.batch))
+    if rank == 0:
+        B[:, 0] = P.B[:, 0]
+    t_gen = time.time() - t_gen
+
+    A = P.A
+    Hd = amg.Hierarchy((torch.from_numpy(A.indptr).to(dev), torch.from_numpy(A.indices).to(dev),
+                        torch.from_numpy(A.data).to(dev)), P.aggs, P.n_nodes, torch.from_numpy(P.W).to(dev))
+    info_h = Hd.info()
+    Bd = torch.from_numpy(B).to(dev)
+    Xd = torch.zeros_like(Bd)
+    o32 = amg.opts(cycle_precision=32, maxit=args.maxit)
+    o64 = amg.opts(cycle_precision=64, maxit=args.maxit)
+    stream = torch.cuda.current_stream()
+
+    def solve_batch():
+        Xd.zero_()
+        return Hd.solve(Bd, Xd, o32)
+
+    # warm-up (also builds the graphs and workspaces)
+    for _ in range(args.warmup):
+        _, infos, st = solve_batch()
+    torch.cuda.synchronize()
+
+    # roofline kernel: auto = the level-0 kernel with the largest share
+    rk = args.roofline_kernel
+    shares = None
+    if rk == "auto" or args.profile_kernels:
+        shares = {}
+        for name, kid in KERNEL_IDS.items():
+            Hd.timer_enable(kid)
+            solve_batch()
+            ms, n = Hd.timer_read()
+            shares[name] = {"ms_total": ms, "launches": n}
+        Hd.timer_enable(0, False)
+        if rk == "auto":
+            rk = max(shares, key=lambda k: shares[k]["ms_total"])
+
+    # one untimed solve with the kernel timer on (its graph is captured here)
+    Hd.timer_enable(KERNEL_IDS[rk])
+    solve_batch()
+    torch.cuda.synchronize()
+    # timed region: device time with CUDA events on the launching stream
+    Hd.timer_enable(KERNEL_IDS[rk])
+    l0 = amg.kernel_launches()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as cs:
+        e0.record(stream)
+        iters = []
+        for _ in range(args.steps):
+            _, infos, st = solve_batch()
+            iters.append([i["iters"] for i in infos])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    launches = amg.kernel_launches() - l0
+    kms, kn = Hd.timer_read()
+    Hd.timer_enable(0, False)
+    elapsed = e0.elapsed_time(e1)
+    elapsed = max_over_ranks(elapsed, ws)
+    per_step = elapsed / args.steps
+    # whole job: ws * batch RHS per step in the slowest rank's time
+    value_job = per_step / (args.batch * ws)
+    print(f"[bench] timed {args.steps} steps: {per_step:.1f} ms/step, iters {iters[0][:4]}..., "
+          f"kernel {rk}: {kms:.2f} ms over {kn} launches, gpu launches {launches}", file=sys.stderr, flush=True)
+    if shares is not None:
+        print(f"[bench] kernel shares {shares}", file=sys.stderr, flush=True)
+    Xc = Xd.cpu().numpy()
+    true_rel = float(max(np.linalg.norm(B[:, c] - A @ Xc[:, c]) / np.linalg.norm(B[:, c]) for c in range(args.batch)))
+
+    # plain float64 solve of one RHS
+    b1 = Bd[:, :1].contiguous()
+    x1 = torch.zeros_like(b1)
+    Hd.solve(b1, x1, o64)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrep = 2
+    f0.record(stream)
+    for _ in range(nrep):
+        x1.zero_()
+        _, inf64, _ = Hd.solve(b1, x1, o64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1) / nrep
+    x64 = x1.cpu().numpy()[:, 0]
+    # the float32-cycle solution of the same RHS against the float64 one
+    err32 = float(np.linalg.norm(Xc[:, 0] - x64) / np.linalg.norm(x64))
+
+    # end to end through the C ABI with host (pinned) buffers
+    Bh = torch.from_numpy(B).pin_memory()
+    Xh = torch.zeros_like(Bh).pin_memory()
+    Hd.solve(Bh, Xh, o32)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    g0.record(stream)
+    for _ in range(2):
+        Xh.zero_()
+        Hd.solve(Bh, Xh, o32)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(g0.elapsed_time(g1) / 2, ws)
+
+    # roofline of the chosen kernel
+    ex1 = Hd.export_level(1)
+    lv = {"n0": P.n, "nnz0": A.nnz, "n1": ex1["n"], "npv1": int(ex1["pval"].size)}
+    wc = 4
+    abytes = algorithmic_bytes(rk, lv, args.batch, wc)
+    avg_ms = kms / max(kn, 1)
+    peak, peak_kind = peaks()
+    achieved = abytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": stored_traffic(rk, f"aniso{args.grid}_K{args.batch}"), "kernel": rk,
+            "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": abytes,
+            "avg_launch_ms": avg_ms, "launches_timed": kn}
+
+    line = {"metric": METRIC, "value": value_job, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-cycle/f64-cg", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rhs_per_step_per_gpu": args.batch, "rtol": 1e-8,
+                       "l2": "inputs larger than L2 (A 113 MB f64 + 75 MB f32, each vector block 268 MB)",
+                       "parallelism": f"replicas x{ws}"},
+            "clocks": cs.summary(), "gpu_launches": launches,
+            "e2e": {"value": e2e_ms / (args.batch), "unit": UNIT,
+                    "h2d_bytes_per_step": int(2 * P.n * args.batch * 8),
+                    "d2h_bytes_per_step": int(P.n * args.batch * 8)},
+            "roofline": roof,
+            "fp64_plain": {"ms_per_rhs": fp64_ms, "iters": inf64[0]["iters"]},
+            "fp32_batched_iters": {"min": int(np.min(iters)), "max": int(np.max(iters))},
+            "fp32_vs_fp64_rel_err": err32, "true_relres_max": true_rel,
+            "speedup_batched_vs_fp64_plain": fp64_ms / value_job if value_job else None,
+            "hierarchy": {"levels": info_h["levels"], "n": info_h["n_level"], "nnz": info_h["nnz_level"],
+                          "opc": info_h["opc"]},
+            "input_gen_s": t_gen}
+    if shares is not None:
+        line["kernel_ms_per_solve"] = shares
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        s = oracle_sample(P, inf64[0]["iters"], args.cpu_sample_s)
+        line["cpu_baseline"] = {"value": s["ms_per_rhs"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{s['sample_iters']} FP64 oracle PCG iterations on the same "
+                                          f"workload (setup untimed, {s['sample_s']:.1f} s), scaled to "
+                                          f"{inf64[0]['iters']} iterations"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    Hd.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

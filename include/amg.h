@@ -199,6 +199,10 @@ enum {
 amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
 amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);
 
+/* Number of kernels this library has launched in the calling process so far
+ * (a kernel replayed from a CUDA graph counts once per replay). */
+amg_status amg_kernel_launches(int64_t* count);
+
 void amg_destroy(amg_handle h);
 
 /* Message of the last failed call on this host thread ("" if none). */

@@ -85,6 +85,7 @@ SIGNATURES = {
                                    C.c_void_p]),
     "amg_timer_enable": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "amg_timer_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "amg_kernel_launches": (C.c_int, [C.POINTER(C.c_int64)]),
     "amg_destroy": (None, [C.c_void_p]),
     "amg_last_error": (C.c_char_p, []),
 }
@@ -108,6 +109,13 @@ def lib():
 
 def last_error() -> str:
     return lib().amg_last_error().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    n = C.c_int64()
+    _check(lib().amg_kernel_launches(C.byref(n)))
+    return n.value
 
 
 def opts(**kw) -> amg_opts:

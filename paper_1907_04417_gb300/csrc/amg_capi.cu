@@ -280,6 +280,12 @@ amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches) {
   return AMG_OK;
 }
 
+amg_status amg_kernel_launches(int64_t* count) {
+  if (!count) return fail(AMG_ERR_INVALID_ARG, "null argument");
+  *count = amg::launches_total();
+  return AMG_OK;
+}
+
 void amg_destroy(amg_handle h) {
   if (!h) return;
   if (h->own) cudaStreamSynchronize(h->own);

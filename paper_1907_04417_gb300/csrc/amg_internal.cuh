@@ -34,7 +34,15 @@ struct Error : std::runtime_error {
     if (!(cond)) throw ::amg::Error(AMG_ERR_INVALID_ARG, msg);                     \
   } while (0)
 
-#define AMG_LAUNCH_CHECK() AMG_CUDA(cudaGetLastError())
+// Every kernel launch of the library goes through AMG_LAUNCH_CHECK, which
+// also counts it (launches recorded into a CUDA graph are counted when the
+// graph is replayed instead).
+void count_launch();
+#define AMG_LAUNCH_CHECK()          \
+  do {                              \
+    AMG_CUDA(cudaGetLastError());   \
+    ::amg::count_launch();          \
+  } while (0)
 
 // ---------------------------------------------------------------- memory --
 // All device memory of a hierarchy (and of its solve workspaces) is taken
@@ -108,24 +116,6 @@ struct Coarsest {
   std::vector<long long> h_inv_off;
 };
 
-// Device-side CG scalars, one entry per (system, column).
-struct CGState {
-  double* rho;
-  double* alpha;
-  double* beta;
-  double* bnorm;
-  double* rnorm;
-  int* conv;
-  int* iters;
-  int* status;
-  int* active_cols;  // per system: number of real columns (nrhs_s)
-  int* done;         // set when every real column stopped
-  int* iter;         // global iteration counter
-  unsigned* counters;
-  double rtol;
-  int maxit;
-};
-
 struct Workspace;
 
 struct Plan {
@@ -192,6 +182,11 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
                 const amg_opts& o, cudaStream_t user);
 void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* x_caller,
                       int nrhs, double* grad, cudaStream_t st);
+
+// launch accounting
+extern thread_local bool g_capturing;
+void add_launches(long long n);
+long long launches_total();
 
 // pointer helpers
 bool is_device_ptr(const void* p);

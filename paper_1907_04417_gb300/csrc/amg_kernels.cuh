@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(BS) k_cg_update(const int* __restrict__ cta_ro
     ldp<double, CPT>(r + e, rv);
     ldv<double, CPT>(p + e, pv);
     ldv<double, CPT>(q + e, qv);
-    double di = __ldg(dinv + e / K);
+    // a one-level hierarchy has no smoother: u0 (and dinv) are then absent
+    double di = u0 ? __ldg(dinv + e / K) : 0.0;
     TC uo[CPT], fo[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(BS) k_cg_update(const int* __restrict__ cta_ro
     }
     stv<double, CPT>(x + e, xv);
     stv<double, CPT>(r + e, rv);
-    stv<TC, CPT>(u0 + e, uo);
+    if (u0) stv<TC, CPT>(u0 + e, uo);
     if (f0) stv<TC, CPT>(f0 + e, fo);
   }
   cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);

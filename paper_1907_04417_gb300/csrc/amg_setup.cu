@@ -3,6 +3,7 @@
 // Section 5), block prolongators, Galerkin coarse matrices, coarse smooth
 // vectors, l1-Jacobi diagonals and the float64 coarsest factorisation.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -10,6 +11,15 @@
 #include "amg_internal.cuh"
 
 namespace amg {
+
+// ----------------------------------------------------- launch accounting --
+static std::atomic<long long> g_launches{0};
+thread_local bool g_capturing = false;
+void count_launch() {
+  if (!g_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------ pointers --
 bool is_device_ptr(const void* p) {

@@ -246,6 +246,8 @@ struct Workspace {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int gchunk = 0, gtimer = -1, gmaxit = -1;
+  long long gkernels = 0;
+  int* h_iter = nullptr;  // pinned
   double grtol = -1;
   std::vector<cudaEvent_t> gev;
   ~Workspace() {
@@ -253,6 +255,7 @@ struct Workspace {
     if (graph) cudaGraphDestroy(graph);
     for (auto e : gev) cudaEventDestroy(e);
     if (h_done) cudaFreeHost(h_done);
+    if (h_iter) cudaFreeHost(h_iter);
   }
 };
 
@@ -329,6 +332,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post) {
   AMG_CUDA(cudaMemset(W->zero_flag, 0, sizeof(int)));
   AMG_CUDA(cudaMemset(ks.done, 0, sizeof(int)));
   AMG_CUDA(cudaMallocHost(&W->h_done, sizeof(int)));
+  AMG_CUDA(cudaMallocHost(&W->h_iter, sizeof(int)));
   W->nzl.resize(P.L);
   for (int k = 0; k < P.L; ++k)
     W->nzl[k] = prec == 64 ? pick_nzl<double>(P.lev[k], K) : pick_nzl<float>(P.lev[k], K);
@@ -354,19 +358,24 @@ struct TimedLaunch {
       AMG_CUDA(cudaEventCreate(&e1));
       pool->push_back(e0);
       pool->push_back(e1);
-      AMG_CUDA(cudaEventRecord(e0, st));
+      // External records become event-record nodes when the stream is captured
+      AMG_CUDA(cudaEventRecordWithFlags(e0, st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
     }
   }
   ~TimedLaunch() {
-    if (on) cudaEventRecord(e1, st);
+    if (on) cudaEventRecordWithFlags(e1, st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   }
 };
 
-static void harvest_events(amg_hierarchy* h, std::vector<cudaEvent_t>& pool, bool destroy) {
+// Adds the device time of the first ``keep`` event pairs of ``pool`` (all
+// pairs when keep < 0) to the handle's timer.
+static void harvest_events(amg_hierarchy* h, std::vector<cudaEvent_t>& pool, bool destroy, long long keep = -1) {
   if (!h) return;
-  for (size_t i = 0; i + 1 < pool.size(); i += 2) {
+  long long pairs = (long long)pool.size() / 2;
+  if (keep >= 0 && keep < pairs) pairs = keep;
+  for (long long i = 0; i < pairs; ++i) {
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) {
       h->timer.total_ms += ms;
       h->timer.launches += 1;
     } else {
@@ -492,7 +501,8 @@ static void enqueue_iteration(amg_hierarchy* h, Plan& P, Workspace& W, cudaStrea
   TC* f0 = (W.prec == 64 || P.L == 1) ? nullptr : static_cast<TC*>(W.f[0]);
   {
     TimedLaunch tl(h, AMG_KERNEL_CG_UPDATE, st, pool);
-    launch_update<TC>(W.K, L0, W.x, W.r, W.p, W.q, static_cast<TC*>(W.u[0]), f0, W.ks, st);
+    TC* u0 = P.L == 1 ? nullptr : static_cast<TC*>(W.u[0]);
+    launch_update<TC>(W.K, L0, W.x, W.r, W.p, W.q, u0, f0, W.ks, st);
   }
   enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
   if (P.L == 1) launch_rz(W, L0, 1, st);
@@ -584,36 +594,54 @@ static void pcg_loop(amg_hierarchy* h, Plan& P, Workspace& W, const amg_opts& o,
       W.gexec = nullptr;
       W.graph = nullptr;
       AMG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      g_capturing = true;
       try {
         for (int c = 0; c < chunk; ++c) enqueue_iteration<TC>(timing ? h : nullptr, P, W, st, timing ? &W.gev : nullptr);
       } catch (...) {
+        g_capturing = false;
         cudaGraph_t g;
         cudaStreamEndCapture(st, &g);
         if (g) cudaGraphDestroy(g);
         throw;
       }
+      g_capturing = false;
       AMG_CUDA(cudaStreamEndCapture(st, &W.graph));
       AMG_CUDA(cudaGraphInstantiate(&W.gexec, W.graph, 0));
+      size_t nn = 0;
+      AMG_CUDA(cudaGraphGetNodes(W.graph, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      AMG_CUDA(cudaGraphGetNodes(W.graph, nodes.data(), &nn));
+      W.gkernels = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        AMG_CUDA(cudaGraphNodeGetType(nd, &ty));
+        if (ty == cudaGraphNodeTypeKernel) ++W.gkernels;
+      }
       W.gchunk = chunk;
       W.gtimer = tkey;
       W.gmaxit = o.maxit;
       W.grtol = o.rtol;
     }
   }
-  int it = 0;
+  int it = 0, done_iters = 0;
   while (true) {
     if (o.use_graph) {
       AMG_CUDA(cudaGraphLaunch(W.gexec, st));
+      add_launches(W.gkernels);
     } else {
       for (int c = 0; c < chunk; ++c) enqueue_iteration<TC>(timing ? h : nullptr, P, W, st, timing ? &pool : nullptr);
     }
     it += chunk;
     AMG_CUDA(cudaMemcpyAsync(W.h_done, W.ks.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA(cudaMemcpyAsync(W.h_iter, W.ks.iter, sizeof(int), cudaMemcpyDeviceToHost, st));
     AMG_CUDA(cudaStreamSynchronize(st));
     if (timing) {
-      if (o.use_graph) harvest_events(h, W.gev, false);
-      else harvest_events(h, pool, true);
+      // iterations of this chunk that did work (the rest exit at once)
+      long long worked = std::max(0, std::min(chunk, *W.h_iter - done_iters));
+      if (o.use_graph) harvest_events(h, W.gev, false, worked);
+      else harvest_events(h, pool, true, worked);
     }
+    done_iters = *W.h_iter;
     if (*W.h_done || it >= o.maxit + chunk) break;
   }
 }
