@@ -199,6 +199,37 @@ enum {
 amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
 amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);
 
+/*
+ * Local bases of Eq. (svd) computed without any device allocation.  The paper
+ * has no counterpart: this entry point exists for callers that may not call
+ * cudaMalloc when they run (a real-time or latency-bound loop where an
+ * allocation can stall the device, a plug-in whose host framework owns every
+ * device allocation, a pipeline held to a pre-reserved memory budget).
+ *
+ * It runs the per-aggregate computation of amg_setup_from_aggregates on
+ * caller-owned device arrays and gives the same bases:
+ *  W          nf x m row-major float64, device: the smooth vectors, with the
+ *             rows of aggregate a at [row_start[a], row_start[a+1]).
+ *  row_start  int32[nagg+1], device, increasing, row_start[nagg] <= nf.
+ *  nf         rows of the level (size(A) in the truncation threshold).
+ *  tol        TOL of the truncation rule.
+ *  U          nf x m row-major float64, device, output: rows of aggregate a
+ *             hold its kept columns 0..r[a]-1 (other columns are not written).
+ *  r          int32[nagg], device, output: kept columns per aggregate.
+ * The only extra memory is a work area of AMG_LOCAL_BASES_STATIC_DOUBLES
+ * doubles (1 MiB) compiled into the library, held by every GPU that loads it
+ * until the process exits; nf * m beyond that size is rejected with
+ * AMG_ERR_INVALID_ARG, as are host pointers and invalid row ranges.  Calls on
+ * one device share the work area: calls that may overlap on the GPU race and
+ * must be ordered by the caller.  The first call on each device looks up the
+ * work area's device address; make it before capturing any stream.  The call
+ * synchronises ``stream`` before returning.
+ */
+#define AMG_LOCAL_BASES_STATIC_DOUBLES (1 << 17)
+amg_status amg_local_bases_static(const double* W, int32_t m, const int32_t* row_start,
+                                  int32_t nagg, int32_t nf, double tol, double* U, int32_t* r,
+                                  void* stream);
+
 /* Number of kernels this library has launched in the calling process so far
  * (a kernel replayed from a CUDA graph counts once per replay). */
 amg_status amg_kernel_launches(int64_t* count);

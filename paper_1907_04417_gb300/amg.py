@@ -86,6 +86,8 @@ SIGNATURES = {
     "amg_timer_enable": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "amg_timer_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amg_kernel_launches": (C.c_int, [C.POINTER(C.c_int64)]),
+    "amg_local_bases_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                         C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "amg_destroy": (None, [C.c_void_p]),
     "amg_last_error": (C.c_char_p, []),
 }
@@ -116,6 +118,19 @@ def kernel_launches() -> int:
     n = C.c_int64()
     _check(lib().amg_kernel_launches(C.byref(n)))
     return n.value
+
+
+def local_bases_static(W, row_start, nf, tol, U, r, stream=None) -> int:
+    """Eq. (svd) bases into caller-owned device tensors without any device
+    allocation (see amg_local_bases_static in include/amg.h).  W, U: (nf, m)
+    float64 CUDA tensors; row_start: (nagg + 1,) int32; r: (nagg,) int32.
+    Returns the amg_status."""
+    keep = []
+    m = int(W.shape[1])
+    nagg = int(row_start.shape[0]) - 1
+    return lib().amg_local_bases_static(_ptr(W, np.float64, keep), m, _ptr(row_start, np.int32, keep), nagg,
+                                        int(nf), float(tol), _ptr(U, np.float64, keep),
+                                        _ptr(r, np.int32, keep), _stream(stream))
 
 
 def opts(**kw) -> amg_opts:
