@@ -66,6 +66,11 @@ typedef struct {
   int32_t use_graph;       /* 1: PCG iterations replayed from a CUDA graph.      1 */
   int32_t check_every;     /* iterations between convergence reads on the host.  8 */
   int32_t autotune;        /* 1: time SpMV lane layouts once per (level, nrhs).  1 */
+  int32_t outer_fp64;      /* float32-cycle mode only.  0: the outer q = A p runs in
+                              double-float arithmetic (hi + lo float pairs with
+                              error-free products and sums, about 2^-44 relative
+                              accuracy) on the float32 pipes; 1: float64 FMAs.
+                              The CG recurrences and dots stay float64 either way. 0 */
 } amg_opts;
 
 /* Per right-hand-side result. */

@@ -48,7 +48,8 @@ class amg_csr(C.Structure):
 class amg_opts(C.Structure):
     _fields_ = [("tol_svd", C.c_double), ("pre", C.c_int32), ("post", C.c_int32),
                 ("cycle_precision", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32),
-                ("use_graph", C.c_int32), ("check_every", C.c_int32), ("autotune", C.c_int32)]
+                ("use_graph", C.c_int32), ("check_every", C.c_int32), ("autotune", C.c_int32),
+                ("outer_fp64", C.c_int32)]
 
 
 class amg_info(C.Structure):

@@ -53,6 +53,7 @@ void amg_default_opts(amg_opts* o) {
   o->use_graph = 1;
   o->check_every = 8;
   o->autotune = 1;
+  o->outer_fp64 = 0;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }

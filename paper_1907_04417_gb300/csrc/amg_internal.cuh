@@ -80,14 +80,12 @@ struct Level {
   int* col = nullptr;
   double* val64 = nullptr;
   float* val32 = nullptr;
+  float* vallo = nullptr;    // level 0: val64 - val32 (the low half of a double-float)
   double* dinv64 = nullptr;  // 1 / sum_j |a_ij|   (non-coarsest levels)
   float* dinv32 = nullptr;
-  // contiguous row ranges, one per CTA, for the row-parallel kernels
-  int ncta = 0;
-  int* cta_row = nullptr;
-  std::vector<int> h_cta_row;
   int max_row_len = 0;
   double avg_row_len = 0;
+  std::vector<int> h_rowptr;  // host copy of rowptr (partitions)
 };
 
 // P^{k+1}: maps level k+1 (coarse) to level k (fine).
@@ -99,11 +97,40 @@ struct Transfer {
   long long* blk_start = nullptr;  // nagg + 1, offsets of the n_a x r_a blocks
   double* p64 = nullptr;
   float* p32 = nullptr;
-  int ncta = 0;                    // aggregate-aligned CTA ranges
-  int* cta_agg = nullptr;
-  int max_rows_cta = 0;
   std::vector<int> h_row_start, h_coarse_start;
   std::vector<long long> h_blk_start;
+};
+
+// Capacities of the shared-memory staging of a CTA's CSR slice (see
+// stage_csr in amg_kernels.cuh).
+struct Stage {
+  int rows_max = 0;  // largest row count of a CTA
+  int span4 = 0;     // capacity of the 4-byte arrays (elements, multiple of 4)
+  int span8 = 0;     // capacity of the 8-byte arrays (elements, multiple of 2)
+  int enabled = 0;   // 0: the level is read straight from global memory
+  int* err = nullptr;
+};
+
+// Aggregate-aligned CTA ranges of one transfer for a given column count, with
+// the largest per-CTA extents (rows, prolongator values, aggregates, coarse
+// dofs) that size the shared-memory staging.
+struct TPart {
+  int ncta = 0;
+  int* cta_agg = nullptr;
+  int rows_max = 0, p_max = 0, a_max = 0, c_max = 0;
+  Stage sg;
+};
+
+// Row ranges of the row-parallel kernels of one level for a given column
+// count (balanced by non-zeros; at level 0 they never straddle two systems),
+// and the fixed groups of CTAs of the two-level deterministic reductions.
+struct RPart {
+  int ncta = 0, ngroups = 0;
+  int* cta_row = nullptr;   // ncta + 1
+  int* grp_cta = nullptr;   // ngroups + 1
+  int* sys_grp = nullptr;   // nsys + 1 (level 0)
+  int* sys_cta = nullptr;   // nsys + 1 (level 0)
+  Stage sg;
 };
 
 // Dense inverses of the coarsest matrix (block-diagonal over systems).
@@ -124,8 +151,6 @@ struct Plan {
   std::vector<Transfer> tr;   // tr[k] maps level k+1 -> level k
   Coarsest co;
   std::vector<int> h_sys_row;  // nsys + 1 level-0 row offsets
-  std::vector<int> h_sys_cta;  // nsys + 1 level-0 CTA offsets
-  int* sys_cta = nullptr;
   int* perm0 = nullptr;        // library row -> row within its own system (caller numbering)
   std::unique_ptr<Arena> arena;
   std::map<long long, std::shared_ptr<Workspace>> ws;
@@ -164,8 +189,6 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
                      const int32_t* n_nodes, const double* W, int m, const amg_opts& o,
                      cudaStream_t st);
 void build_batch_plan(Plan& out, const std::vector<amg_hierarchy*>& hs, cudaStream_t st);
-void make_row_partition(Plan& P, int k, int target_rows, const std::vector<int>& sys_rows,
-                        cudaStream_t st);
 
 // solve (amg_solve.cu)
 struct SolveReq {

@@ -69,20 +69,145 @@ __device__ __forceinline__ void stv(T* p, const T (&r)[N]) {
   }
 }
 
+// ------------------------------------------------ TMA bulk staging --
+// A CTA's rows [r0, r1) own the contiguous non-zeros [rowptr[r0], rowptr[r1]).
+// One thread copies that slice of col (and of each value array) into shared
+// memory with 1-D bulk TMA copies (cp.async.bulk, completion on an mbarrier)
+// while the CTA loads its rowptr slice; the row loops then take indices and
+// values from shared memory and only the x gathers go to L2/HBM.  Copies are
+// widened to 16-byte boundaries (the arrays carry 16 padding elements).
+// The wait on the mbarrier is bounded: on timeout the kernel records an error
+// in *err (the host then reports AMG_ERR_TIMEOUT) and waits once more, with
+// the same bound, before it goes on.
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+// Shared memory of the staging area with n4 four-byte and n8 eight-byte value arrays.
+__host__ __device__ inline size_t stage_bytes(const Stage& sg, int n4, int n8) {
+  if (!sg.enabled) return 0;
+  return 16 + align16((size_t)(sg.rows_max + 1) * 4) + (size_t)sg.span4 * 4 * (1 + n4) +
+         (size_t)sg.span8 * 8 * n8;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  if (bytes == 0) return;
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
+  unsigned ok = 0;
+  for (int it = 0; it < (1 << 22) && !ok; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+  }
+  return ok != 0;
+}
+
+// Where the row loop reads rowptr / col / values: either the staged copies
+// (with index offsets) or the global arrays.
+template <typename TA>
+struct CsrView {
+  const int* rp;
+  int roff;
+  const int* col;
+  int coff;
+  const TA* val;
+  int voff;
+};
+
+// Stage rows [r0, r1): col plus NV value arrays of widths vw[] (4 or 8).
+template <int NV>
+__device__ __forceinline__ bool stage_csr(const Stage& sg, unsigned char* smem, int r0, int r1,
+                                          const int* __restrict__ rowptr, const int* __restrict__ col,
+                                          const void* const (&vsrc)[NV], const int (&vw)[NV],
+                                          const void* (&vdst)[NV], const int*& srp, const int*& scol,
+                                          int& j4, int& j8) {
+  if (!sg.enabled) return false;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  int* rp_s = reinterpret_cast<int*>(smem + 16);
+  int* col_s = reinterpret_cast<int*>(smem + 16 + align16((size_t)(sg.rows_max + 1) * 4));
+  unsigned char* vp = reinterpret_cast<unsigned char*>(col_s + sg.span4);
+  const int j0 = __ldg(rowptr + r0), j1 = __ldg(rowptr + r1);
+  j4 = j0 & ~3;
+  j8 = j0 & ~1;
+  const int e4 = (j1 + 3) & ~3, e8 = (j1 + 1) & ~1;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    vdst[a] = vp;
+    vp += vw[a] == 4 ? (size_t)sg.span4 * 4 : (size_t)sg.span8 * 8;
+  }
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned b4 = (unsigned)(e4 - j4) * 4u, b8 = (unsigned)(e8 - j8) * 8u;
+    unsigned total = b4;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) total += vw[a] == 4 ? b4 : b8;
+    mbar_expect_tx(bar, total);
+    tma_load_1d(col_s, col + j4, b4, bar);
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const unsigned char* src = static_cast<const unsigned char*>(vsrc[a]);
+      if (vw[a] == 4) tma_load_1d(const_cast<void*>(vdst[a]), src + (size_t)j4 * 4, b4, bar);
+      else tma_load_1d(const_cast<void*>(vdst[a]), src + (size_t)j8 * 8, b8, bar);
+    }
+  }
+  for (int t = threadIdx.x; t <= r1 - r0; t += blockDim.x) rp_s[t] = __ldg(rowptr + r0 + t);
+  __syncthreads();
+  if (!mbar_wait_bounded(bar, 0)) {
+    atomicOr(sg.err, 1);
+    mbar_wait_bounded(bar, 0);
+  }
+  srp = rp_s;
+  scol = col_s;
+  return true;
+}
+
 // y_i = sum_j a_ij x_j for the K columns owned by this lane.
 template <typename TA, typename TX, int K, int NZL>
-__device__ __forceinline__ void row_acc(int i, bool valid, const int* __restrict__ rowptr,
-                                        const int* __restrict__ col, const TA* __restrict__ val,
-                                        const TX* __restrict__ x, int nzl, int cl,
-                                        TX (&acc)[VT<TX, K>::CPT]) {
+__device__ __forceinline__ void row_acc(int i, bool valid, const CsrView<TA>& cv, const TX* __restrict__ x,
+                                        int nzl, int cl, TX (&acc)[VT<TX, K>::CPT]) {
   constexpr int CPT = VT<TX, K>::CPT, CL = VT<TX, K>::CL;
 #pragma unroll
   for (int t = 0; t < CPT; ++t) acc[t] = TX(0);
   if (valid) {
-    int j1 = __ldg(rowptr + i + 1);
-    for (int j = __ldg(rowptr + i) + nzl; j < j1; j += NZL) {
-      TX a = (TX)__ldg(val + j);
-      int c = __ldg(col + j);
+    const int j1 = cv.rp[i + 1 - cv.roff];
+    int j = cv.rp[i - cv.roff] + nzl;
+    // four non-zeros at a time: their gathers are independent and issue
+    // back to back
+    for (; j + 3 * NZL < j1; j += 4 * NZL) {
+      int c[4];
+      TX a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = cv.col[j + u * NZL - cv.coff];
+        a[u] = (TX)cv.val[j + u * NZL - cv.voff];
+      }
+      TX xv[4][CPT];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ldv<TX, CPT>(x + (size_t)c[u] * K + cl * CPT, xv[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) acc[t] = fma(a[u], xv[u][t], acc[t]);
+    }
+    for (; j < j1; j += NZL) {
+      TX a = (TX)cv.val[j - cv.voff];
+      int c = cv.col[j - cv.coff];
       TX xv[CPT];
       ldv<TX, CPT>(x + (size_t)c * K + cl * CPT, xv);
 #pragma unroll
@@ -95,6 +220,22 @@ __device__ __forceinline__ void row_acc(int i, bool valid, const int* __restrict
 #pragma unroll
       for (int t = 0; t < CPT; ++t) acc[t] += __shfl_xor_sync(FULL, acc[t], off);
   }
+}
+
+// Stage one value array of type TA and build the view the row loop reads.
+template <typename TA>
+__device__ __forceinline__ CsrView<TA> staged_view(const Stage& sg, unsigned char* smem, int r0, int r1,
+                                                   const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                   const TA* __restrict__ val) {
+  const void* src[1] = {val};
+  const int w[1] = {(int)sizeof(TA)};
+  const void* dst[1];
+  const int* srp;
+  const int* scol;
+  int j4, j8;
+  if (stage_csr<1>(sg, smem, r0, r1, rowptr, col, src, w, dst, srp, scol, j4, j8))
+    return CsrView<TA>{srp, r0, scol, j4, static_cast<const TA*>(dst[0]), sizeof(TA) == 4 ? j4 : j8};
+  return CsrView<TA>{rowptr, 0, col, 0, val, 0};
 }
 
 // Sum the per-lane column partials of one CTA into out[0..K) (smem scratch
@@ -119,17 +260,61 @@ __device__ __forceinline__ void cta_colsum(double (&d)[CPT], double* sm, double*
   }
 }
 
+// ------------------------------------------------------- double-float --
+// A value v is carried as an unevaluated sum hi + lo of two floats (hi =
+// fl32(v)).  Products use the exact FMA residual of the leading product plus
+// the two cross terms; sums use Knuth's two-sum followed by a fast two-sum.
+// The result keeps about 44 bits, all on the float32 pipes.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+// (sh, sl) += (ah, al) * (xh, xl)
+__device__ __forceinline__ void df_mac(float ah, float al, float xh, float xl, float& sh, float& sl) {
+  float ph = ah * xh;
+  float pl = fmaf(ah, xh, -ph);
+  pl = fmaf(ah, xl, fmaf(al, xh, pl));
+  float s, e;
+  df_two_sum(sh, ph, s, e);
+  e += sl + pl;
+  df_fast_two_sum(s, e, sh, sl);
+}
+// (sh, sl) += (oh, ol)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
+  float s, e;
+  df_two_sum(sh, oh, s, e);
+  e += sl + ol;
+  df_fast_two_sum(s, e, sh, sl);
+}
+__device__ __forceinline__ void df_split(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
 // CG scalars shared by the fused kernels.
 struct KState {
-  double* partial;     // ncta0 * NV
+  double* partial;     // ncta0 * NV   (one row per CTA)
+  double* gpartial;    // ngroups * NV (one row per group of CTAs)
   unsigned* counter;   // one counter per reducing kernel
+  unsigned* gcount;    // per reducing kernel: one counter per group
+  const int* grp_cta;  // ngroups + 1
+  const int* sys_grp;  // nsys + 1
+  int ngroups;
   double *rho, *alpha, *beta, *bnorm, *rnorm;
   int *conv, *iters, *status, *active, *done, *iter;
   const int* sys_cta;  // nsys + 1
   int nsys;
   double rtol;
   int maxit;
+  Stage sg;            // level-0 staging of the reducing SpMV kernels
 };
+
+enum : int { RED_Q = 0, RED_UPDATE = 1, RED_POST = 2, RED_INIT = 3, RED_KINDS = 4 };
 
 enum : int { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_BREAKDOWN = 2, ST_MAXIT = 3 };
 
@@ -141,20 +326,6 @@ __device__ __forceinline__ int cta_system(const int* sys_cta, int nsys) {
     if (__ldg(sys_cta + mid) <= b) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-// Returns true in the last CTA to finish; that CTA then sees all partials.
-__device__ __forceinline__ bool arrive_last(unsigned* counter) {
-  __shared__ int last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
 }
 
 // Deterministic sum of partial[b*NV + v] over b in [b0, b1) for v < NV
@@ -174,6 +345,47 @@ __device__ __forceinline__ void sum_partials(const double* partial, int NV, int 
   __syncthreads();
 }
 
+// Two-level deterministic reduction: each CTA has written its NV partials;
+// the last CTA of each fixed group sums the group (in CTA order), and the
+// last group to finish returns true with every group sum in ks.gpartial.
+__device__ __forceinline__ bool arrive_two_level(const KState& ks, int kind, int NV, double* sm, double* tot) {
+  __shared__ int flag;
+  int lo = 0, hi = ks.ngroups - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(ks.grp_cta + mid) <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int g = lo, b0 = ks.grp_cta[g], b1 = ks.grp_cta[g + 1];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(ks.gcount + kind * ks.ngroups + g, 1u);
+    flag = (prev == (unsigned)(b1 - b0 - 1));
+  }
+  __syncthreads();
+  if (!flag) return false;
+  __threadfence();
+  sum_partials(ks.partial, NV, b0, b1, sm, tot);
+  if (threadIdx.x < NV) ks.gpartial[(size_t)g * NV + threadIdx.x] = tot[threadIdx.x];
+  if (threadIdx.x == 0) ks.gcount[kind * ks.ngroups + g] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(ks.counter + kind, 1u);
+    flag = (prev == (unsigned)(ks.ngroups - 1));
+  }
+  __syncthreads();
+  if (!flag) return false;
+  __threadfence();
+  if (threadIdx.x == 0) ks.counter[kind] = 0u;
+  return true;
+}
+
+// Per-system totals of the group sums (final CTA only).
+__device__ __forceinline__ void system_totals(const KState& ks, int NV, int sy, double* sm, double* tot) {
+  sum_partials(ks.gpartial, NV, ks.sys_grp[sy], ks.sys_grp[sy + 1], sm, tot);
+}
+
 // ------------------------------------------------------------ V-cycle ----
 
 // v = u + D^{-1} (f - A u)   (one l1-Jacobi sweep, out of place)
@@ -182,28 +394,63 @@ __global__ void __launch_bounds__(BS) k_smooth(const int* __restrict__ cta_row, 
                                                const int* __restrict__ col, const TC* __restrict__ val,
                                                const TC* __restrict__ dinv, const TC* __restrict__ f,
                                                const TC* __restrict__ u, TC* __restrict__ v,
-                                               const int* __restrict__ done) {
+                                               const int* __restrict__ done, Stage sg) {
   if (*done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, G = NZL * CL, RPW = 32 / G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
   const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
+  const CsrView<TC> cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
     bool valid = i < r1;
-    TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, rowptr, col, val, u, nzl, cl, acc);
+    const size_t o = (size_t)i * K + cl * CPT;
+    TC fv[CPT], uv[CPT];
     if (valid && nzl == 0) {
-      TC fv[CPT], uv[CPT], out[CPT];
-      size_t o = (size_t)i * K + cl * CPT;
       ldv<TC, CPT>(f + o, fv);
       ldv<TC, CPT>(u + o, uv);
+    }
+    TC acc[CPT];
+    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
+    if (valid && nzl == 0) {
+      TC out[CPT];
       TC di = __ldg(dinv + i);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[t], uv[t]);
       stv<TC, CPT>(v + o, out);
     }
   }
+}
+
+// Shared-memory layout of the transfer kernels: [vector tile | P tile |
+// per-aggregate row, coarse-dof and block offsets | dof -> aggregate map].
+template <typename TC>
+__host__ __device__ inline size_t transfer_smem(int rows_max, int p_max, int a_max, int c_max, int K,
+                                                bool with_tile) {
+  return (with_tile ? align16((size_t)rows_max * K * sizeof(TC)) : 0) + align16((size_t)p_max * sizeof(TC)) +
+         (size_t)3 * (a_max + 1) * sizeof(int) + (size_t)(c_max > rows_max ? c_max : rows_max) * sizeof(int);
+}
+template <typename TC>
+__host__ __device__ inline size_t restrict_stage_bytes(const Stage& sg) {
+  return stage_bytes(sg, sizeof(TC) == 4 ? 1 : 0, sizeof(TC) == 8 ? 1 : 0);
+}
+
+// Stage the CTA's aggregate metadata and its (contiguous) prolongator blocks.
+template <typename TC>
+__device__ __forceinline__ void stage_transfer(int a0, int a1, const int* __restrict__ row_start,
+                                               const int* __restrict__ coarse_start,
+                                               const long long* __restrict__ blk_start,
+                                               const TC* __restrict__ P, TC* psm, int* m_rs, int* m_cs,
+                                               int* m_bk) {
+  const int r0 = row_start[a0], c0 = coarse_start[a0];
+  const long long b0 = blk_start[a0], b1 = blk_start[a1];
+  for (int t = threadIdx.x; t <= a1 - a0; t += BS) {
+    m_rs[t] = __ldg(row_start + a0 + t) - r0;
+    m_cs[t] = __ldg(coarse_start + a0 + t) - c0;
+    m_bk[t] = (int)(__ldg(blk_start + a0 + t) - b0);
+  }
+  for (long long e = threadIdx.x; e < b1 - b0; e += BS) psm[e] = __ldg(P + b0 + e);
 }
 
 // Fused residual + restriction on aggregate-aligned CTAs:
@@ -219,48 +466,56 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
                                                  const TC* __restrict__ val, const TC* __restrict__ f,
                                                  const TC* __restrict__ u, TC* __restrict__ fc,
                                                  TC* __restrict__ uc, const TC* __restrict__ dinvc,
-                                                 const int* __restrict__ done) {
+                                                 const int* __restrict__ done, int rows_max, int p_max,
+                                                 int a_max, Stage sg) {
   if (*done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  TC* tsm = reinterpret_cast<TC*>(smraw);
+  unsigned char* tail = smraw + restrict_stage_bytes<TC>(sg);
+  TC* tsm = reinterpret_cast<TC*>(tail);
+  TC* psm = reinterpret_cast<TC*>(tail + align16((size_t)rows_max * K * sizeof(TC)));
+  int* m_rs = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(psm) + align16((size_t)p_max * sizeof(TC)));
+  int* m_cs = m_rs + (a_max + 1);
+  int* m_bk = m_cs + (a_max + 1);
+  int* cd2a = m_bk + (a_max + 1);
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, G = NZL * CL, RPW = 32 / G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
   const int a0 = cta_agg[blockIdx.x], a1 = cta_agg[blockIdx.x + 1];
   const int r0 = row_start[a0], r1 = row_start[a1];
+  stage_transfer<TC>(a0, a1, row_start, coarse_start, blk_start, P, psm, m_rs, m_cs, m_bk);
+  __syncthreads();
+  const CsrView<TC> cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
+  for (int t = threadIdx.x; t < a1 - a0; t += BS)
+    for (int p = m_cs[t]; p < m_cs[t + 1]; ++p) cd2a[p] = t;
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
     bool valid = i < r1;
+    const size_t o = (size_t)i * K + cl * CPT;
+    TC fv[CPT];
+    if (valid && nzl == 0) ldv<TC, CPT>(f + o, fv);
     TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, rowptr, col, val, u, nzl, cl, acc);
+    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
     if (valid && nzl == 0) {
-      TC fv[CPT];
-      size_t o = (size_t)i * K + cl * CPT;
-      ldv<TC, CPT>(f + o, fv);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) fv[t] -= acc[t];
       stv<TC, CPT>(tsm + (size_t)(i - r0) * K + cl * CPT, fv);
     }
   }
   __syncthreads();
-  const int c0 = coarse_start[a0], c1 = coarse_start[a1];
-  const int nout = (c1 - c0) * K;
+  const int c0 = coarse_start[a0];
+  const int nout = m_cs[a1 - a0] * K;
   for (int o = threadIdx.x; o < nout; o += BS) {
-    int cd = c0 + o / K, c = o % K;
-    int lo = a0, hi = a1 - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (__ldg(coarse_start + mid) <= cd) lo = mid; else hi = mid - 1;
-    }
-    int a = lo;
-    int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
-    int rs = __ldg(row_start + a), na = __ldg(row_start + a + 1) - rs;
-    const TC* pa = P + __ldg(blk_start + a) + (cd - cs);
-    const TC* ta = tsm + (size_t)(rs - r0) * K + c;
+    int cdl = o / K, c = o % K;
+    int t = cd2a[cdl];
+    int p = cdl - m_cs[t], ra = m_cs[t + 1] - m_cs[t];
+    int rsl = m_rs[t], na = m_rs[t + 1] - rsl;
+    const TC* pa = psm + m_bk[t] + p;
+    const TC* ta = tsm + (size_t)rsl * K + c;
     TC s = TC(0);
-    for (int i = 0; i < na; ++i) s = fma(__ldg(pa + (size_t)i * ra), ta[(size_t)i * K], s);
-    fc[(size_t)cd * K + c] = s;
-    if (uc) uc[(size_t)cd * K + c] = s * __ldg(dinvc + cd);
+    for (int i = 0; i < na; ++i) s = fma(pa[i * ra], ta[(size_t)i * K], s);
+    size_t oc = (size_t)(c0 + cdl) * K + c;
+    fc[oc] = s;
+    if (uc) uc[oc] = s * __ldg(dinvc + c0 + cdl);
   }
 }
 
@@ -270,37 +525,45 @@ __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg,
                                                 const int* __restrict__ coarse_start,
                                                 const long long* __restrict__ blk_start, const TC* __restrict__ P,
                                                 const TC* __restrict__ uc, TC* __restrict__ u,
-                                                const int* __restrict__ done) {
+                                                const int* __restrict__ done, int rows_max, int p_max,
+                                                int a_max) {
   if (*done) return;
-  constexpr int CPT = VT<TC, K>::CPT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TC* psm = reinterpret_cast<TC*>(smraw);
+  int* m_rs = reinterpret_cast<int*>(smraw + align16((size_t)p_max * sizeof(TC)));
+  int* m_cs = m_rs + (a_max + 1);
+  int* m_bk = m_cs + (a_max + 1);
+  int* r2a = m_bk + (a_max + 1);
+  constexpr int CPT = VT<TC, K>::CPT, NV = K / CPT;
   const int a0 = cta_agg[blockIdx.x], a1 = cta_agg[blockIdx.x + 1];
-  const int r0 = row_start[a0], r1 = row_start[a1];
-  const int nout = (r1 - r0) * (K / CPT);
+  const int r0 = row_start[a0], c0 = coarse_start[a0];
+  stage_transfer<TC>(a0, a1, row_start, coarse_start, blk_start, P, psm, m_rs, m_cs, m_bk);
+  __syncthreads();
+  for (int t = threadIdx.x; t < a1 - a0; t += BS)
+    for (int il = m_rs[t]; il < m_rs[t + 1]; ++il) r2a[il] = t;
+  __syncthreads();
+  const int nout = m_rs[a1 - a0] * NV;
   for (int o = threadIdx.x; o < nout; o += BS) {
-    int i = r0 + o / (K / CPT), c = (o % (K / CPT)) * CPT;
-    int lo = a0, hi = a1 - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (__ldg(row_start + mid) <= i) lo = mid; else hi = mid - 1;
-    }
-    int a = lo;
-    int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
-    const TC* pr = P + __ldg(blk_start + a) + (size_t)(i - __ldg(row_start + a)) * ra;
+    int il = o / NV, c = (o % NV) * CPT;
+    int t = r2a[il];
+    int ra = m_cs[t + 1] - m_cs[t];
+    const TC* pr = psm + m_bk[t] + (il - m_rs[t]) * ra;
+    const TC* ucp = uc + (size_t)(c0 + m_cs[t]) * K + c;
     TC s[CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) s[t] = TC(0);
+    for (int q = 0; q < CPT; ++q) s[q] = TC(0);
     for (int p = 0; p < ra; ++p) {
-      TC pv = __ldg(pr + p);
+      TC pv = pr[p];
       TC cv[CPT];
-      ldv<TC, CPT>(uc + (size_t)(cs + p) * K + c, cv);
+      ldv<TC, CPT>(ucp + (size_t)p * K, cv);
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) s[t] = fma(pv, cv[t], s[t]);
+      for (int q = 0; q < CPT; ++q) s[q] = fma(pv, cv[q], s[q]);
     }
-    TC* up = u + (size_t)i * K + c;
+    TC* up = u + (size_t)(r0 + il) * K + c;
     TC uv[CPT];
     ldp<TC, CPT>(up, uv);
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) uv[t] += s[t];
+    for (int q = 0; q < CPT; ++q) uv[q] += s[q];
     stv<TC, CPT>(up, uv);
   }
 }
@@ -355,6 +618,44 @@ __global__ void __launch_bounds__(BS) k_coarse(int n, int nblk, const int* __res
 // x += alpha p; r -= alpha q; ||r||^2; then the first pre-sweep of the
 // V-cycle from zero, u0 = D^{-1} r, and f0 = r in the cycle precision.  The
 // last CTA applies the stopping test of every (system, column).
+// Last CTA of an update launch: the stopping test of every active column
+// (||r|| <= rtol ||b||, non-finite -> breakdown, iteration limit), the
+// iteration counter and the all-stopped flag.
+template <int K>
+__device__ __forceinline__ void finish_update(KState& ks, double* sm, double* tot) {
+  const int it = *ks.iter + 1;
+  for (int sy = 0; sy < ks.nsys; ++sy) {
+    system_totals(ks, K, sy, sm, tot);
+    if (threadIdx.x < K) {
+      int v = sy * K + threadIdx.x;
+      if (ks.conv[v] == ST_ACTIVE) {
+        double rn = sqrt(tot[threadIdx.x]);
+        ks.rnorm[v] = rn;
+        if (!isfinite(rn)) {
+          ks.conv[v] = ST_BREAKDOWN;
+          ks.status[v] = AMG_ERR_BREAKDOWN;
+          ks.iters[v] = it;
+        } else if (rn <= ks.rtol * ks.bnorm[v]) {
+          ks.conv[v] = ST_CONVERGED;
+          ks.iters[v] = it;
+        } else if (it >= ks.maxit) {
+          ks.conv[v] = ST_MAXIT;
+          ks.status[v] = AMG_ERR_NOT_CONVERGED;
+          ks.iters[v] = it;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int stopped = 1;
+    for (int v = 0; v < ks.nsys * K; ++v)
+      if (ks.conv[v] == ST_ACTIVE) stopped = 0;
+    *ks.iter = it;
+    if (stopped) *ks.done = 1;
+  }
+}
+
 template <typename TC, int K>
 __global__ void __launch_bounds__(BS) k_cg_update(const int* __restrict__ cta_row, double* __restrict__ x,
                                                   double* __restrict__ r, const double* __restrict__ p,
@@ -394,39 +695,8 @@ __global__ void __launch_bounds__(BS) k_cg_update(const int* __restrict__ cta_ro
     if (f0) stv<TC, CPT>(f0 + e, fo);
   }
   cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
-  if (!arrive_last(ks.counter + 1)) return;
-  const int it = *ks.iter + 1;
-  int stopped = 1;
-  for (int sy = 0; sy < ks.nsys; ++sy) {
-    sum_partials(ks.partial, K, ks.sys_cta[sy], ks.sys_cta[sy + 1], sm, tot);
-    if (threadIdx.x < K) {
-      int v = sy * K + threadIdx.x;
-      if (ks.conv[v] == ST_ACTIVE) {
-        double rn = sqrt(tot[threadIdx.x]);
-        ks.rnorm[v] = rn;
-        if (!isfinite(rn)) {
-          ks.conv[v] = ST_BREAKDOWN;
-          ks.status[v] = AMG_ERR_BREAKDOWN;
-          ks.iters[v] = it;
-        } else if (rn <= ks.rtol * ks.bnorm[v]) {
-          ks.conv[v] = ST_CONVERGED;
-          ks.iters[v] = it;
-        } else if (it >= ks.maxit) {
-          ks.conv[v] = ST_MAXIT;
-          ks.status[v] = AMG_ERR_NOT_CONVERGED;
-          ks.iters[v] = it;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    for (int v = 0; v < ks.nsys * K; ++v)
-      if (ks.conv[v] == ST_ACTIVE) stopped = 0;
-    *ks.iter = it;
-    if (stopped) *ks.done = 1;
-    *(ks.counter + 1) = 0u;
-  }
+  if (!arrive_two_level(ks, RED_UPDATE, K, sm, tot)) return;
+  finish_update<K>(ks, sm, tot);
 }
 
 // First pre-sweep from zero on level 0 (used after the initial residual).
@@ -456,48 +726,92 @@ __global__ void __launch_bounds__(BS) k_presmooth0(const int* __restrict__ cta_r
 //   z = u + D^{-1} (f - A u),
 // fused with r.z.  mode 0: rho = r.z (start); mode 1: beta = r.z / rho,
 // rho = r.z; mode 2: no scalars (a bare V-cycle).
-template <typename TC, int K, int NZL>
-__global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+template <typename TC, int K, int NZL, bool DF>
+__global__ void __launch_bounds__(BS, 5) k_post0(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                               const int* __restrict__ col, const TC* __restrict__ val,
                                               const TC* __restrict__ dinv, const TC* __restrict__ f,
                                               const TC* __restrict__ u, const double* __restrict__ r,
-                                              double* __restrict__ z, KState ks, int mode) {
+                                              const float* __restrict__ rlo, TC* __restrict__ z, KState ks,
+                                              int mode, Stage sg) {
   if (*ks.done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
   __shared__ double tot[64];
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, G = NZL * CL, RPW = 32 / G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
   const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
-  double d[CPT];
+  // DF: r = f + rlo exactly (double-float CG) and r.z is accumulated in
+  // double-float; otherwise r is float64
+  constexpr int ND = DF ? 1 : CPT, NF = DF ? CPT : 1;
+  double d[ND];
+  float dh[NF], dl[NF];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) d[t] = 0;
+  for (int t = 0; t < ND; ++t) d[t] = 0;
+#pragma unroll
+  for (int t = 0; t < NF; ++t) dh[t] = dl[t] = 0.f;
+  const CsrView<TC> cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
     bool valid = i < r1;
-    TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, rowptr, col, val, u, nzl, cl, acc);
+    const size_t o = (size_t)i * K + cl * CPT;
+    // the row's own operands are loaded before its gathers so that their
+    // misses overlap
+    TC fv[CPT], uv[CPT];
+    float lv[NF];
     if (valid && nzl == 0) {
-      TC fv[CPT], uv[CPT];
-      size_t o = (size_t)i * K + cl * CPT;
       ldv<TC, CPT>(f + o, fv);
       ldv<TC, CPT>(u + o, uv);
+      if constexpr (DF) ldv<float, CPT>(rlo + o, lv);
+    }
+    TC acc[CPT];
+    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
+    if constexpr (DF) {
+      if (valid && nzl == 0) {
+        TC zt[CPT];
+        TC di = __ldg(dinv + i);
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+          zt[t] = fma(di, fv[t] - acc[t], uv[t]);
+          df_mac((float)fv[t], lv[t], (float)zt[t], 0.f, dh[t], dl[t]);
+        }
+        stv<TC, CPT>(z + o, zt);
+      }
+    } else if (valid && nzl == 0) {
       TC di = __ldg(dinv + i);
+      TC zt[CPT];
+      double rv[CPT];
+      if constexpr (CPT >= 2) {
+#pragma unroll
+        for (int t = 0; t < CPT; t += 2) {
+          double two[2];
+          ldv<double, 2>(r + o + t, two);
+          rv[t] = two[0];
+          rv[t + 1] = two[1];
+        }
+      } else {
+        rv[0] = __ldg(r + o);
+      }
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
-        double zv = (double)fma(di, fv[t] - acc[t], uv[t]);
-        double rv = __ldg(r + o + t);
-        z[o + t] = zv;
-        d[t] = fma(rv, zv, d[t]);
+        zt[t] = fma(di, fv[t] - acc[t], uv[t]);
+        d[t] = fma(rv[t], (double)zt[t], d[t]);
       }
+      stv<TC, CPT>(z + o, zt);
     }
   }
   if (mode == 2) return;
+  double dd[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    if constexpr (DF) dd[t] = (double)dh[t] + (double)dl[t];
+    else dd[t] = d[t];
+  }
   // lanes other than nzl == 0 hold zeros; reduce across the whole warp
-  cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
-  if (!arrive_last(ks.counter + 2)) return;
+  cta_colsum<K, CPT>(dd, sm, ks.partial + (size_t)blockIdx.x * K);
+  if (!arrive_two_level(ks, RED_POST, K, sm, tot)) return;
   for (int sy = 0; sy < ks.nsys; ++sy) {
-    sum_partials(ks.partial, K, ks.sys_cta[sy], ks.sys_cta[sy + 1], sm, tot);
+    system_totals(ks, K, sy, sm, tot);
     if (threadIdx.x < K) {
       int v = sy * K + threadIdx.x;
       double rz = tot[threadIdx.x];
@@ -523,7 +837,6 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
     for (int v = 0; v < ks.nsys * K; ++v)
       if (ks.conv[v] == ST_ACTIVE) stopped = 0;
     if (stopped) *ks.done = 1;
-    *(ks.counter + 2) = 0u;
   }
 }
 

@@ -85,36 +85,47 @@ inline void ensure_smem(Kern k, size_t bytes) {
 }
 
 template <typename TC>
-void launch_smooth(int K, int nzl, const Level& L, const TC* f, const TC* u, TC* v, const int* done,
-                   cudaStream_t st);
+void launch_smooth(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u, TC* v,
+                   const int* done, cudaStream_t st);
 template <typename TC>
-void launch_restrict(int K, int nzl, const Level& L, const Transfer& T, const Level& C, bool smooth_next,
-                     const TC* f, const TC* u, TC* fc, TC* uc, const int* done, cudaStream_t st);
+void launch_restrict(int K, int nzl, const Level& L, const Transfer& T, const TPart& tp, const Level& C,
+                     bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, const int* done,
+                     cudaStream_t st);
 template <typename TC>
-void launch_prolong(int K, const Transfer& T, const TC* uc, TC* u, const int* done, cudaStream_t st);
+void launch_prolong(int K, const Transfer& T, const TPart& tp, const TC* uc, TC* u, const int* done,
+                    cudaStream_t st);
 template <typename TC>
 void launch_coarse(int K, const Coarsest& C, const TC* f, TC* u, const int* done, cudaStream_t st);
 template <typename TC>
-void launch_post0(int K, int nzl, const Level& L, const TC* f, const TC* u, const double* r, double* z,
-                  const KState& ks, int mode, cudaStream_t st);
+void launch_post0(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u, const double* r,
+                  const float* rlo, TC* z, const KState& ks, int mode, cudaStream_t st);
 template <typename TC>
-void launch_update(int K, const Level& L, double* x, double* r, const double* p, const double* q, TC* u0,
-                   TC* f0, const KState& ks, cudaStream_t st);
+void launch_update(int K, const Level& L, const RPart& rp, double* x, double* r, const double* p,
+                   const double* q, TC* u0, TC* f0, const KState& ks, cudaStream_t st);
 template <typename TC>
-void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, const int* done,
-                       cudaStream_t st);
+void launch_presmooth0(int K, const Level& L, const RPart& rp, const double* r, TC* u0, TC* f0,
+                       const int* done, cudaStream_t st);
+
+// shared memory of a staged SpMV kernel reading one value array of type TC
+template <typename TC>
+inline size_t csr_stage_bytes(const Stage& sg) {
+  return stage_bytes(sg, sizeof(TC) == 4 ? 1 : 0, sizeof(TC) == 8 ? 1 : 0);
+}
 
 #define AMG_DEFINE_LAUNCHERS(TC)                                                                       \
   template <>                                                                                          \
-  void launch_smooth<TC>(int K, int nzl, const Level& L, const TC* f, const TC* u, TC* v,              \
-                         const int* done, cudaStream_t st) {                                           \
+  void launch_smooth<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,   \
+                         TC* v, const int* done, cudaStream_t st) {                                    \
+    size_t smem = csr_stage_bytes<TC>(rp.sg);                                                          \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
       dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
         constexpr int NZ = decltype(nc)::value;                                                        \
         if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
-          k_smooth<TC, KK, NZ><<<L.ncta, BS, 0, st>>>(L.cta_row, L.rowptr, L.col, vals<TC>(L),        \
-                                                      dinvs<TC>(L), f, u, v, done);                    \
+          auto kern = k_smooth<TC, KK, NZ>;                                                            \
+          ensure_smem(kern, smem);                                                                     \
+          kern<<<rp.ncta, BS, smem, st>>>(rp.cta_row, L.rowptr, L.col, vals<TC>(L), dinvs<TC>(L), f,   \
+                                          u, v, done, rp.sg);                                          \
         } else {                                                                                       \
           throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
         }                                                                                              \
@@ -123,10 +134,11 @@ void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, c
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
   template <>                                                                                          \
-  void launch_restrict<TC>(int K, int nzl, const Level& L, const Transfer& T, const Level& C,          \
-                           bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc,                 \
+  void launch_restrict<TC>(int K, int nzl, const Level& L, const Transfer& T, const TPart& tp,         \
+                           const Level& C, bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, \
                            const int* done, cudaStream_t st) {                                         \
-    size_t smem = (size_t)T.max_rows_cta * K * sizeof(TC);                                             \
+    size_t smem = restrict_stage_bytes<TC>(tp.sg) +                                                    \
+                  transfer_smem<TC>(tp.rows_max, tp.p_max, tp.a_max, tp.c_max, K, true);              \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
       dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
@@ -134,10 +146,11 @@ void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, c
         if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
           auto kern = k_restrict<TC, KK, NZ>;                                                          \
           ensure_smem(kern, smem);                                                                     \
-          kern<<<T.ncta, BS, smem, st>>>(T.cta_agg, T.row_start, T.coarse_start, T.blk_start,          \
-                                         pvals<TC>(T), L.rowptr, L.col, vals<TC>(L), f, u, fc,         \
-                                         smooth_next ? uc : nullptr,                                   \
-                                         smooth_next ? dinvs<TC>(C) : nullptr, done);                  \
+          kern<<<tp.ncta, BS, smem, st>>>(tp.cta_agg, T.row_start, T.coarse_start, T.blk_start,        \
+                                          pvals<TC>(T), L.rowptr, L.col, vals<TC>(L), f, u, fc,        \
+                                          smooth_next ? uc : nullptr,                                  \
+                                          smooth_next ? dinvs<TC>(C) : nullptr, done, tp.rows_max,     \
+                                          tp.p_max, tp.a_max, tp.sg);                                  \
         } else {                                                                                       \
           throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
         }                                                                                              \
@@ -146,12 +159,15 @@ void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, c
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
   template <>                                                                                          \
-  void launch_prolong<TC>(int K, const Transfer& T, const TC* uc, TC* u, const int* done,              \
-                          cudaStream_t st) {                                                           \
+  void launch_prolong<TC>(int K, const Transfer& T, const TPart& tp, const TC* uc, TC* u,             \
+                          const int* done, cudaStream_t st) {                                          \
+    size_t smem = transfer_smem<TC>(tp.rows_max, tp.p_max, tp.a_max, tp.c_max, K, false);             \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
-      k_prolong<TC, KK><<<T.ncta, BS, 0, st>>>(T.cta_agg, T.row_start, T.coarse_start, T.blk_start,   \
-                                               pvals<TC>(T), uc, u, done);                             \
+      auto kern = k_prolong<TC, KK>;                                                                   \
+      ensure_smem(kern, smem);                                                                         \
+      kern<<<tp.ncta, BS, smem, st>>>(tp.cta_agg, T.row_start, T.coarse_start, T.blk_start,            \
+                                      pvals<TC>(T), uc, u, done, tp.rows_max, tp.p_max, tp.a_max);     \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
@@ -166,15 +182,19 @@ void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, c
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
   template <>                                                                                          \
-  void launch_post0<TC>(int K, int nzl, const Level& L, const TC* f, const TC* u, const double* r,     \
-                        double* z, const KState& ks, int mode, cudaStream_t st) {                      \
+  void launch_post0<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,    \
+                        const double* r, const float* rlo, TC* z, const KState& ks, int mode,          \
+                        cudaStream_t st) {                                                             \
+    size_t smem = csr_stage_bytes<TC>(rp.sg);                                                          \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
       dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
         constexpr int NZ = decltype(nc)::value;                                                        \
         if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
-          k_post0<TC, KK, NZ><<<L.ncta, BS, 0, st>>>(L.cta_row, L.rowptr, L.col, vals<TC>(L),         \
-                                                     dinvs<TC>(L), f, u, r, z, ks, mode);              \
+          auto kern = rlo ? k_post0<TC, KK, NZ, true> : k_post0<TC, KK, NZ, false>;                    \
+          ensure_smem(kern, smem);                                                                     \
+          kern<<<rp.ncta, BS, smem, st>>>(rp.cta_row, L.rowptr, L.col, vals<TC>(L), dinvs<TC>(L), f,   \
+                                          u, r, rlo, z, ks, mode, rp.sg);                              \
         } else {                                                                                       \
           throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
         }                                                                                              \
@@ -183,20 +203,21 @@ void launch_presmooth0(int K, const Level& L, const double* r, TC* u0, TC* f0, c
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
   template <>                                                                                          \
-  void launch_update<TC>(int K, const Level& L, double* x, double* r, const double* p,                 \
-                         const double* q, TC* u0, TC* f0, const KState& ks, cudaStream_t st) {         \
+  void launch_update<TC>(int K, const Level& L, const RPart& rp, double* x, double* r,                 \
+                         const double* p, const double* q, TC* u0, TC* f0, const KState& ks,           \
+                         cudaStream_t st) {                                                            \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
-      k_cg_update<TC, KK><<<L.ncta, BS, 0, st>>>(L.cta_row, x, r, p, q, L.dinv64, u0, f0, ks);        \
+      k_cg_update<TC, KK><<<rp.ncta, BS, 0, st>>>(rp.cta_row, x, r, p, q, L.dinv64, u0, f0, ks);      \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
   template <>                                                                                          \
-  void launch_presmooth0<TC>(int K, const Level& L, const double* r, TC* u0, TC* f0,                   \
+  void launch_presmooth0<TC>(int K, const Level& L, const RPart& rp, const double* r, TC* u0, TC* f0,  \
                              const int* done, cudaStream_t st) {                                       \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
-      k_presmooth0<TC, KK><<<L.ncta, BS, 0, st>>>(L.cta_row, r, L.dinv64, u0, f0, done);              \
+      k_presmooth0<TC, KK><<<rp.ncta, BS, 0, st>>>(rp.cta_row, r, L.dinv64, u0, f0, done);            \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }

@@ -50,6 +50,15 @@ static std::vector<T> to_host(const T* p, size_t n, cudaStream_t st) {
   return v;
 }
 
+// Non-zero arrays are padded by 16 elements (zeroed) so that 16-byte
+// aligned bulk copies of a row range may run past its last entry.
+template <typename T>
+static T* alloc_nnz(Arena& ar, long long nnz, cudaStream_t st) {
+  T* p = ar.alloc<T>(nnz + 16);
+  AMG_CUDA(cudaMemsetAsync(p + nnz, 0, 16 * sizeof(T), st));
+  return p;
+}
+
 template <typename T>
 static T* to_dev(Arena& ar, const std::vector<T>& v, cudaStream_t st) {
   T* d = ar.alloc<T>(v.size() ? v.size() : 1);
@@ -409,6 +418,13 @@ __global__ void k_l1(int n, const int* __restrict__ rowptr, const double* __rest
   d32[i] = (float)(1.0 / s);
 }
 
+// lo = a - (double)(float)a as a float: (val32, lo) is a double-float pair.
+__global__ void k_split_lo(long long n, const double* __restrict__ a, const float* __restrict__ hi,
+                           float* __restrict__ lo) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) lo[i] = (float)(a[i] - (double)hi[i]);
+}
+
 template <typename TI, typename TO>
 __global__ void k_cast(long long n, const TI* __restrict__ in, TO* __restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -498,71 +514,12 @@ static void check_flag(int* dflag, cudaStream_t st, const char* what) {
   if (f & 4) throw Error(AMG_ERR_INVALID_ARG, std::string(what) + ": a row has no non-zero entry (zero l1 norm) or a non-finite value");
 }
 
-void make_row_partition(Plan& P, int k, int target_rows, const std::vector<int>& sys_rows,
-                        cudaStream_t st) {
-  Level& L = P.lev[k];
-  std::vector<int> cr;
-  std::vector<int> sys_cta;
-  cr.push_back(0);
-  sys_cta.push_back(0);
-  for (size_t s = 0; s + 1 < sys_rows.size(); ++s) {
-    int r0 = sys_rows[s], r1 = sys_rows[s + 1];
-    int nr = r1 - r0;
-    int nc = std::max(1, (nr + target_rows - 1) / target_rows);
-    for (int c = 1; c <= nc; ++c) cr.push_back(r0 + (int)((long long)nr * c / nc));
-    sys_cta.push_back((int)cr.size() - 1);
-  }
-  L.h_cta_row = cr;
-  L.ncta = (int)cr.size() - 1;
-  L.cta_row = to_dev(*P.arena, cr, st);
-  if (k == 0) {
-    P.h_sys_cta = sys_cta;
-    P.sys_cta = to_dev(*P.arena, sys_cta, st);
-  }
-}
-
-static int rows_per_cta(int n) {
-  // about four CTAs per SM on a 152-SM part, at least 64 rows per CTA
-  int t = (n + 607) / 608;
-  return std::max(64, t);
-}
-
-static void make_transfer_partition(Plan& P, int k, int target_rows, cudaStream_t st) {
-  Transfer& T = P.tr[k];
-  std::vector<int> ca;
-  ca.push_back(0);
-  int rows = 0, maxr = 0, start_row = 0;
-  for (int a = 0; a < T.nagg; ++a) {
-    int na = T.h_row_start[a + 1] - T.h_row_start[a];
-    if (rows > 0 && rows + na > target_rows) {
-      ca.push_back(a);
-      maxr = std::max(maxr, rows);
-      rows = 0;
-    }
-    rows += na;
-    (void)start_row;
-  }
-  ca.push_back(T.nagg);
-  maxr = std::max(maxr, rows);
-  T.ncta = (int)ca.size() - 1;
-  T.max_rows_cta = maxr;
-  T.cta_agg = to_dev(*P.arena, ca, st);
-}
-
 static void level_stats(Level& L, const std::vector<int>& rp) {
+  L.h_rowptr = rp;
   int mx = 0;
   for (int i = 0; i < L.n; ++i) mx = std::max(mx, rp[i + 1] - rp[i]);
   L.max_row_len = mx;
   L.avg_row_len = L.n ? (double)L.nnz / L.n : 0;
-}
-
-static void finish_partitions(Plan& P, cudaStream_t st) {
-  for (int k = 0; k < P.L; ++k) {
-    std::vector<int> sys = {0, P.lev[k].n};
-    if (k == 0) sys = P.h_sys_row;
-    make_row_partition(P, k, rows_per_cta(P.lev[k].n), sys, st);
-  }
-  for (int k = 0; k + 1 < P.L; ++k) make_transfer_partition(P, k, 256, st);
 }
 
 // Dense inverse of the coarsest matrix (one block).
@@ -674,8 +631,8 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
     if (!is_device_ptr(A->col)) { int* t = tmp.alloc<int>(A->nnz); copy_in(t, A->col, (size_t)A->nnz * 4, st); d_col = t; }
     if (!is_device_ptr(A->val)) { double* t = tmp.alloc<double>(A->nnz); copy_in(t, A->val, (size_t)A->nnz * 8, st); d_val = t; }
     L0.rowptr = to_dev(ar, rpn, st);
-    L0.col = ar.alloc<int>(A->nnz);
-    L0.val64 = ar.alloc<double>(A->nnz);
+    L0.col = alloc_nnz<int>(ar, A->nnz, st);
+    L0.val64 = alloc_nnz<double>(ar, A->nnz, st);
     h->nzmap = ar.alloc<int>(A->nnz);
     P.perm0 = to_dev(ar, perm[0], st);
     int* d_iperm = tmp.alloc<int>(n);
@@ -802,8 +759,8 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
     C.n = ncoarse;
     C.nnz = nnzc;
     C.rowptr = to_dev(ar, rpc, st);
-    C.col = ar.alloc<int>(nnzc);
-    C.val64 = ar.alloc<double>(nnzc);
+    C.col = alloc_nnz<int>(ar, nnzc, st);
+    C.val64 = alloc_nnz<double>(ar, nnzc, st);
     level_stats(C, rpc);
     k_gal_cols<<<nagg, 128, 0, st>>>(nagg, T.coarse_start, d_nbp, d_nbl, C.rowptr, C.col);
     AMG_LAUNCH_CHECK();
@@ -830,9 +787,14 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
     F.dinv32 = ar.alloc<float>(nf);
     k_l1<<<grid_for(nf, 256), 256, 0, st>>>(nf, F.rowptr, F.val64, F.dinv64, F.dinv32, dflag);
     AMG_LAUNCH_CHECK();
-    F.val32 = ar.alloc<float>(F.nnz);
+    F.val32 = alloc_nnz<float>(ar, F.nnz, st);
     k_cast<double, float><<<grid_for(F.nnz, 256), 256, 0, st>>>(F.nnz, F.val64, F.val32);
     AMG_LAUNCH_CHECK();
+    if (k == 1) {
+      F.vallo = alloc_nnz<float>(ar, F.nnz, st);
+      k_split_lo<<<grid_for(F.nnz, 256), 256, 0, st>>>(F.nnz, F.val64, F.val32, F.vallo);
+      AMG_LAUNCH_CHECK();
+    }
     k_cast<double, float><<<grid_for(T.npval, 256), 256, 0, st>>>(T.npval, T.p64, T.p32);
     AMG_LAUNCH_CHECK();
     check_flag(dflag, st, "level setup");
@@ -843,9 +805,14 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
   }
   // coarsest level: float32 copy (for exports) and dense inverse
   Level& C = P.lev[L - 1];
-  C.val32 = ar.alloc<float>(C.nnz);
+  C.val32 = alloc_nnz<float>(ar, C.nnz, st);
   k_cast<double, float><<<grid_for(C.nnz, 256), 256, 0, st>>>(C.nnz, C.val64, C.val32);
   AMG_LAUNCH_CHECK();
+  if (L == 1) {
+    C.vallo = alloc_nnz<float>(ar, C.nnz, st);
+    k_split_lo<<<grid_for(C.nnz, 256), 256, 0, st>>>(C.nnz, C.val64, C.val32, C.vallo);
+    AMG_LAUNCH_CHECK();
+  }
   P.co.n = C.n;
   P.co.nblk = 1;
   P.co.h_blk_off = {0, C.n};
@@ -854,7 +821,6 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
   P.co.inv_off = to_dev(ar, P.co.h_inv_off, st);
   P.co.inv = ar.alloc<double>((size_t)C.n * C.n);
   coarsest_inverse(P, C, P.co.inv, st, dflag);
-  finish_partitions(P, st);
   AMG_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -885,9 +851,10 @@ void build_batch_plan(Plan& B, const std::vector<amg_hierarchy*>& hs, cudaStream
     D.n = n;
     D.nnz = nnz;
     D.rowptr = ar.alloc<int>(n + 1);
-    D.col = ar.alloc<int>(nnz);
-    D.val64 = ar.alloc<double>(nnz);
-    D.val32 = ar.alloc<float>(nnz);
+    D.col = alloc_nnz<int>(ar, nnz, st);
+    D.val64 = alloc_nnz<double>(ar, nnz, st);
+    D.val32 = alloc_nnz<float>(ar, nnz, st);
+    if (k == 0) D.vallo = alloc_nnz<float>(ar, nnz, st);
     bool coarse = (k == L - 1);
     if (!coarse) {
       D.dinv64 = ar.alloc<double>(n);
@@ -904,6 +871,7 @@ void build_batch_plan(Plan& B, const std::vector<amg_hierarchy*>& hs, cudaStream
       AMG_LAUNCH_CHECK();
       AMG_CUDA(cudaMemcpyAsync(D.val64 + zo, S.val64, S.nnz * 8, cudaMemcpyDeviceToDevice, st));
       AMG_CUDA(cudaMemcpyAsync(D.val32 + zo, S.val32, S.nnz * 4, cudaMemcpyDeviceToDevice, st));
+      if (k == 0) AMG_CUDA(cudaMemcpyAsync(D.vallo + zo, S.vallo, S.nnz * 4, cudaMemcpyDeviceToDevice, st));
       if (!coarse) {
         AMG_CUDA(cudaMemcpyAsync(D.dinv64 + ro, S.dinv64, S.n * 8, cudaMemcpyDeviceToDevice, st));
         AMG_CUDA(cudaMemcpyAsync(D.dinv32 + ro, S.dinv32, S.n * 4, cudaMemcpyDeviceToDevice, st));
@@ -914,6 +882,12 @@ void build_batch_plan(Plan& B, const std::vector<amg_hierarchy*>& hs, cudaStream
     }
     D.max_row_len = mx;
     D.avg_row_len = n ? (double)nnz / n : 0;
+    D.h_rowptr.assign(1, 0);
+    for (auto* h : hs) {
+      const Level& S = h->plan.lev[k];
+      long long base = D.h_rowptr.back();
+      for (int i = 1; i <= S.n; ++i) D.h_rowptr.push_back((int)(base + S.h_rowptr[i]));
+    }
   }
   for (int k = 0; k + 1 < L; ++k) {
     Transfer& T = B.tr[k];
@@ -972,7 +946,6 @@ void build_batch_plan(Plan& B, const std::vector<amg_hierarchy*>& hs, cudaStream
   for (int s = 0; s < ns; ++s)
     AMG_CUDA(cudaMemcpyAsync(B.perm0 + B.h_sys_row[s], hs[s]->plan.perm0, hs[s]->plan.lev[0].n * 4,
                              cudaMemcpyDeviceToDevice, st));
-  finish_partitions(B, st);
   AMG_CUDA(cudaStreamSynchronize(st));
 }
 

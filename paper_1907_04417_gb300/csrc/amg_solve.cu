@@ -11,39 +11,12 @@ namespace amg {
 
 // ------------------------------------------------------- float64 kernels --
 
-// q = A p with p.q; the last CTA forms alpha = rho / p.q per column.
-template <int K, int NZL>
-__global__ void __launch_bounds__(BS) k_cg_q(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
-                                             const int* __restrict__ col, const double* __restrict__ val,
-                                             const double* __restrict__ p, double* __restrict__ q, KState ks) {
-  if (*ks.done) return;
-  __shared__ double sm[BS];
-  __shared__ double tot[64];
-  constexpr int CPT = VT<double, K>::CPT, CL = VT<double, K>::CL, G = NZL * CL, RPW = 32 / G;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
-  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
-  double d[CPT];
-#pragma unroll
-  for (int t = 0; t < CPT; ++t) d[t] = 0;
-  for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
-    int i = base + g;
-    bool valid = i < r1;
-    double acc[CPT];
-    row_acc<double, double, K, NZL>(i, valid, rowptr, col, val, p, nzl, cl, acc);
-    if (valid && nzl == 0) {
-      size_t o = (size_t)i * K + cl * CPT;
-      double pv[CPT];
-      ldv<double, CPT>(p + o, pv);
-      stv<double, CPT>(q + o, acc);
-#pragma unroll
-      for (int t = 0; t < CPT; ++t) d[t] = fma(pv[t], acc[t], d[t]);
-    }
-  }
-  cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
-  if (!arrive_last(ks.counter + 0)) return;
+// Last CTA of a q = A p launch: alpha = rho / p.q for every active column;
+// p.q <= 0 or a non-finite alpha stops the column with a breakdown.
+template <int K>
+__device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot) {
   for (int sy = 0; sy < ks.nsys; ++sy) {
-    sum_partials(ks.partial, K, ks.sys_cta[sy], ks.sys_cta[sy + 1], sm, tot);
+    system_totals(ks, K, sy, sm, tot);
     if (threadIdx.x < K) {
       int v = sy * K + threadIdx.x;
       double pq = tot[threadIdx.x];
@@ -61,7 +34,147 @@ __global__ void __launch_bounds__(BS) k_cg_q(const int* __restrict__ cta_row, co
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *(ks.counter + 0) = 0u;
+}
+
+// q = A p in double-float on the float32 pipes: A as (val32, vallo), p as
+// (ph, pl), every product and sum error-free up to the final rounding of
+// the pair; q is stored in float64 and p.q is accumulated in double-float.
+template <int K, int NZL>
+__global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+                                                const int* __restrict__ col, const float* __restrict__ ahi,
+                                                const float* __restrict__ alo, const float* __restrict__ ph,
+                                                const float* __restrict__ pl, float* __restrict__ qh,
+                                                float* __restrict__ ql, KState ks) {
+  if (*ks.done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sm[BS];
+  __shared__ double tot[64];
+  constexpr int CPT = VT<float, K>::CPT, CL = VT<float, K>::CL, G = NZL * CL, RPW = 32 / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
+  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
+  float dh[CPT], dl[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) dh[t] = dl[t] = 0.f;
+  // stage col, val_hi and val_lo of the CTA's rows
+  const int* rp = rowptr;
+  const int* cc = col;
+  const float* va = ahi;
+  const float* vb = alo;
+  int roff = 0, joff = 0;
+  {
+    const void* src[2] = {ahi, alo};
+    const int w[2] = {4, 4};
+    const void* dst[2];
+    const int *srp, *scol;
+    int j4, j8;
+    if (stage_csr<2>(ks.sg, smraw, r0, r1, rowptr, col, src, w, dst, srp, scol, j4, j8)) {
+      rp = srp;
+      cc = scol;
+      va = static_cast<const float*>(dst[0]);
+      vb = static_cast<const float*>(dst[1]);
+      roff = r0;
+      joff = j4;
+    }
+  }
+  for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
+    int i = base + g;
+    bool valid = i < r1;
+    const size_t o = (size_t)i * K + cl * CPT;
+    float hv[CPT], lv[CPT];
+    if (valid && nzl == 0) {
+      ldv<float, CPT>(ph + o, hv);
+      ldv<float, CPT>(pl + o, lv);
+    }
+    float sh[CPT], sl[CPT];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) sh[t] = sl[t] = 0.f;
+    if (valid) {
+      int j1 = rp[i + 1 - roff] - joff;
+      int j = rp[i - roff] - joff + nzl;
+      for (; j + NZL < j1; j += 2 * NZL) {  // two non-zeros in flight
+        int c0 = cc[j], c1 = cc[j + NZL];
+        float ah0 = va[j], al0 = vb[j];
+        float ah1 = va[j + NZL], al1 = vb[j + NZL];
+        float xh0[CPT], xl0[CPT], xh1[CPT], xl1[CPT];
+        ldv<float, CPT>(ph + (size_t)c0 * K + cl * CPT, xh0);
+        ldv<float, CPT>(pl + (size_t)c0 * K + cl * CPT, xl0);
+        ldv<float, CPT>(ph + (size_t)c1 * K + cl * CPT, xh1);
+        ldv<float, CPT>(pl + (size_t)c1 * K + cl * CPT, xl1);
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+          df_mac(ah0, al0, xh0[t], xl0[t], sh[t], sl[t]);
+          df_mac(ah1, al1, xh1[t], xl1[t], sh[t], sl[t]);
+        }
+      }
+      for (; j < j1; j += NZL) {
+        float ah = va[j], al = vb[j];
+        int c = cc[j];
+        float xh[CPT], xl[CPT];
+        ldv<float, CPT>(ph + (size_t)c * K + cl * CPT, xh);
+        ldv<float, CPT>(pl + (size_t)c * K + cl * CPT, xl);
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) df_mac(ah, al, xh[t], xl[t], sh[t], sl[t]);
+      }
+    }
+    if constexpr (NZL > 1) {
+#pragma unroll
+      for (int off = CL; off < CL * NZL; off <<= 1)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+          float oh = __shfl_xor_sync(FULL, sh[t], off), ol = __shfl_xor_sync(FULL, sl[t], off);
+          df_add(sh[t], sl[t], oh, ol);
+        }
+    }
+    if (valid && nzl == 0) {
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) df_mac(hv[t], lv[t], sh[t], sl[t], dh[t], dl[t]);
+      stv<float, CPT>(qh + o, sh);
+      stv<float, CPT>(ql + o, sl);
+    }
+  }
+  double d[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) d[t] = (double)dh[t] + (double)dl[t];
+  cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
+  if (!arrive_two_level(ks, RED_Q, K, sm, tot)) return;
+  finish_alpha<K>(ks, sm, tot);
+}
+
+// q = A p with p.q; the last CTA forms alpha = rho / p.q per column.
+template <int K, int NZL>
+__global__ void __launch_bounds__(BS) k_cg_q(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+                                             const int* __restrict__ col, const double* __restrict__ val,
+                                             const double* __restrict__ p, double* __restrict__ q, KState ks) {
+  if (*ks.done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sm[BS];
+  __shared__ double tot[64];
+  constexpr int CPT = VT<double, K>::CPT, CL = VT<double, K>::CL, G = NZL * CL, RPW = 32 / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
+  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
+  double d[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) d[t] = 0;
+  const CsrView<double> cv = staged_view<double>(ks.sg, smraw, r0, r1, rowptr, col, val);
+  for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
+    int i = base + g;
+    bool valid = i < r1;
+    double acc[CPT];
+    row_acc<double, double, K, NZL>(i, valid, cv, p, nzl, cl, acc);
+    if (valid && nzl == 0) {
+      size_t o = (size_t)i * K + cl * CPT;
+      double pv[CPT];
+      ldv<double, CPT>(p + o, pv);
+      stv<double, CPT>(q + o, acc);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) d[t] = fma(pv[t], acc[t], d[t]);
+    }
+  }
+  cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
+  if (!arrive_two_level(ks, RED_Q, K, sm, tot)) return;
+  finish_alpha<K>(ks, sm, tot);
 }
 
 // r = b - A x with ||b||^2 and ||r||^2; the last CTA initialises the state
@@ -72,6 +185,7 @@ __global__ void __launch_bounds__(BS) k_cg_init(const int* __restrict__ cta_row,
                                                 const int* __restrict__ col, const double* __restrict__ val,
                                                 const double* __restrict__ b, const double* __restrict__ x,
                                                 double* __restrict__ r, KState ks) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
   __shared__ double tot[64];
   constexpr int CPT = VT<double, K>::CPT, CL = VT<double, K>::CL, G = NZL * CL, RPW = 32 / G;
@@ -81,11 +195,12 @@ __global__ void __launch_bounds__(BS) k_cg_init(const int* __restrict__ cta_row,
   double db[CPT], dr[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) db[t] = dr[t] = 0;
+  const CsrView<double> cv = staged_view<double>(ks.sg, smraw, r0, r1, rowptr, col, val);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
     bool valid = i < r1;
     double acc[CPT];
-    row_acc<double, double, K, NZL>(i, valid, rowptr, col, val, x, nzl, cl, acc);
+    row_acc<double, double, K, NZL>(i, valid, cv, x, nzl, cl, acc);
     if (valid && nzl == 0) {
       size_t o = (size_t)i * K + cl * CPT;
       double bv[CPT], rv[CPT];
@@ -102,9 +217,9 @@ __global__ void __launch_bounds__(BS) k_cg_init(const int* __restrict__ cta_row,
   cta_colsum<K, CPT>(db, sm, ks.partial + (size_t)blockIdx.x * 2 * K);
   __syncthreads();
   cta_colsum<K, CPT>(dr, sm, ks.partial + (size_t)blockIdx.x * 2 * K + K);
-  if (!arrive_last(ks.counter + 3)) return;
+  if (!arrive_two_level(ks, RED_INIT, 2 * K, sm, tot)) return;
   for (int sy = 0; sy < ks.nsys; ++sy) {
-    sum_partials(ks.partial, 2 * K, ks.sys_cta[sy], ks.sys_cta[sy + 1], sm, tot);
+    system_totals(ks, 2 * K, sy, sm, tot);
     if (threadIdx.x < K) {
       int v = sy * K + threadIdx.x;
       double bn = sqrt(tot[threadIdx.x]), rn = sqrt(tot[K + threadIdx.x]);
@@ -131,14 +246,16 @@ __global__ void __launch_bounds__(BS) k_cg_init(const int* __restrict__ cta_row,
       if (ks.conv[v] == ST_ACTIVE) stopped = 0;
     *ks.done = stopped;
     *ks.iter = 0;
-    *(ks.counter + 3) = 0u;
   }
 }
 
-// p = z + beta p
-template <int K>
-__global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, const double* __restrict__ z,
-                                             double* __restrict__ p, KState ks) {
+// p = z + beta p; with SPLIT, p lives as the double-float pair (ph, pl)
+// read by the double-float q = A p.
+// z is stored in the cycle precision TZ; ``first`` starts the recurrence
+// (p = z, the previous p is not read).
+template <int K, typename TZ>
+__global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, const TZ* __restrict__ z,
+                                             double* __restrict__ p, KState ks, int first) {
   if (*ks.done) return;
   AMG_ELEMENTWISE_PROLOGUE(double)
   const int s = cta_system(ks.sys_cta, ks.nsys);
@@ -146,13 +263,137 @@ __global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, co
 #pragma unroll
   for (int t = 0; t < CPT; ++t) be[t] = ks.beta[s * K + cfirst + t];
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
-    double zv[CPT], pv[CPT];
-    ldv<double, CPT>(z + e, zv);
-    ldp<double, CPT>(p + e, pv);
+    TZ zt[CPT];
+    double pv[CPT];
+    ldv<TZ, CPT>(z + e, zt);
+    if (first) {
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) pv[t] = fma(be[t], pv[t], zv[t]);
+      for (int t = 0; t < CPT; ++t) pv[t] = (double)zt[t];
+    } else {
+      ldp<double, CPT>(p + e, pv);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) pv[t] = fma(be[t], pv[t], (double)zt[t]);
+    }
     stv<double, CPT>(p + e, pv);
   }
+}
+
+// ------------------------------------------------ double-float CG vectors --
+// In the float32-cycle mode x, r, p and q are kept as double-float pairs
+// (hi, lo) and every CG vector operation runs on the float32 pipes; the CG
+// scalars (alpha, beta, rho, norms) stay float64.  r_hi = fl32(r) is then
+// exactly the float32 right-hand side of the level-0 cycle.
+
+__device__ __forceinline__ void split2(double v, float& h, float& l) { df_split(v, h, l); }
+
+// x += alpha p, r -= alpha q, ||r||^2; u0 = D^{-1} r_hi (first pre-sweep).
+template <int K>
+__global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta_row, float* __restrict__ xh,
+                                                     float* __restrict__ xl, float* __restrict__ rh,
+                                                     float* __restrict__ rl, const float* __restrict__ ph,
+                                                     const float* __restrict__ pl, const float* __restrict__ qh,
+                                                     const float* __restrict__ ql, const float* __restrict__ dinv,
+                                                     float* __restrict__ u0, KState ks) {
+  if (*ks.done) return;
+  __shared__ double sm[BS];
+  __shared__ double tot[64];
+  constexpr int CPT = VT<float, K>::CPT;
+  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
+  const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
+  const int cfirst = (int)((threadIdx.x * CPT) % K);
+  const int s = cta_system(ks.sys_cta, ks.nsys);
+  float ah[CPT], al[CPT], dh[CPT], dl[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+    dh[t] = dl[t] = 0.f;
+  }
+  for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
+    float xa[CPT], xb[CPT], ra[CPT], rb[CPT], pa[CPT], pb[CPT], qa[CPT], qb[CPT], uo[CPT];
+    ldp<float, CPT>(xh + e, xa);
+    ldp<float, CPT>(xl + e, xb);
+    ldp<float, CPT>(rh + e, ra);
+    ldp<float, CPT>(rl + e, rb);
+    ldv<float, CPT>(ph + e, pa);
+    ldv<float, CPT>(pl + e, pb);
+    ldv<float, CPT>(qh + e, qa);
+    ldv<float, CPT>(ql + e, qb);
+    float di = __ldg(dinv + e / K);
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      df_mac(ah[t], al[t], pa[t], pb[t], xa[t], xb[t]);
+      df_mac(-ah[t], -al[t], qa[t], qb[t], ra[t], rb[t]);
+      df_mac(ra[t], rb[t], ra[t], rb[t], dh[t], dl[t]);
+      uo[t] = di * ra[t];
+    }
+    stv<float, CPT>(xh + e, xa);
+    stv<float, CPT>(xl + e, xb);
+    stv<float, CPT>(rh + e, ra);
+    stv<float, CPT>(rl + e, rb);
+    stv<float, CPT>(u0 + e, uo);
+  }
+  double d[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) d[t] = (double)dh[t] + (double)dl[t];
+  cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
+  if (!arrive_two_level(ks, RED_UPDATE, K, sm, tot)) return;
+  finish_update<K>(ks, sm, tot);
+}
+
+// p = z + beta p on the double-float pair (first: p = z).
+template <int K>
+__global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
+                                                float* __restrict__ ph, float* __restrict__ pl, KState ks,
+                                                int first) {
+  if (*ks.done) return;
+  constexpr int CPT = VT<float, K>::CPT;
+  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
+  const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
+  const int cfirst = (int)((threadIdx.x * CPT) % K);
+  const int s = cta_system(ks.sys_cta, ks.nsys);
+  float bh[CPT], bl[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) split2(ks.beta[s * K + cfirst + t], bh[t], bl[t]);
+  for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
+    float zv[CPT], pa[CPT], pb[CPT];
+    ldv<float, CPT>(z + e, zv);
+    if (first) {
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        pa[t] = zv[t];
+        pb[t] = 0.f;
+      }
+    } else {
+      ldp<float, CPT>(ph + e, pa);
+      ldp<float, CPT>(pl + e, pb);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        float sh = zv[t], sl = 0.f;
+        df_mac(bh[t], bl[t], pa[t], pb[t], sh, sl);
+        pa[t] = sh;
+        pb[t] = sl;
+      }
+    }
+    stv<float, CPT>(ph + e, pa);
+    stv<float, CPT>(pl + e, pb);
+  }
+}
+
+// float64 <-> double-float pairs (start and end of a solve)
+__global__ void k_split_pair(long long n, const double* __restrict__ v, float* __restrict__ h,
+                             float* __restrict__ l) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) df_split(v[i], h[i], l[i]);
+}
+__global__ void k_join_pair(long long n, const float* __restrict__ h, const float* __restrict__ l,
+                            double* __restrict__ v) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (double)h[i] + (double)l[i];
+}
+
+__global__ void k_f32_to_f64(long long n, const float* __restrict__ a, double* __restrict__ b) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
 }
 
 // One-level hierarchy (the coarsest is the fine level): r.z after z = A^{-1} r.
@@ -175,9 +416,9 @@ __global__ void __launch_bounds__(BS) k_rz(const int* __restrict__ cta_row, cons
     for (int t = 0; t < CPT; ++t) d[t] = fma(rv[t], zv[t], d[t]);
   }
   cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
-  if (!arrive_last(ks.counter + 2)) return;
+  if (!arrive_two_level(ks, RED_POST, K, sm, tot)) return;
   for (int sy = 0; sy < ks.nsys; ++sy) {
-    sum_partials(ks.partial, K, ks.sys_cta[sy], ks.sys_cta[sy + 1], sm, tot);
+    system_totals(ks, K, sy, sm, tot);
     if (threadIdx.x < K) {
       int v = sy * K + threadIdx.x;
       double rz = tot[threadIdx.x];
@@ -193,7 +434,6 @@ __global__ void __launch_bounds__(BS) k_rz(const int* __restrict__ cta_row, cons
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) *(ks.counter + 2) = 0u;
 }
 
 // caller (n_s x nrhs, own numbering) -> library (n x K, padded with zeros)
@@ -236,6 +476,9 @@ struct Workspace {
   int K = 0, prec = 64, n0 = 0, L = 0, pre = 1, post = 1;
   Arena ar;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
+  bool split = false;  // double-float CG vectors (float32-cycle mode)
+  float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr;
+  float *ph = nullptr, *pl = nullptr, *qh = nullptr, *ql = nullptr;
   std::vector<void*> f, u, v;
   KState ks{};
   int* zero_flag = nullptr;
@@ -243,6 +486,10 @@ struct Workspace {
   size_t stage_elems = 0;
   int* h_done = nullptr;  // pinned
   std::vector<int> nzl;   // per level
+  int nzl_q = 0;          // lanes per row of the level-0 q = A p
+  std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
+  std::vector<RPart> rp;  // per level: row ranges for this column count
+  int* err = nullptr;     // bounded-wait failures of the staged kernels
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int gchunk = 0, gtimer = -1, gmaxit = -1;
@@ -274,14 +521,188 @@ static int pick_nzl(const Level& L, int K) {
   return std::min(v, mx);
 }
 
+// Aggregate-aligned CTA ranges holding about ``target`` rows each (an
+// aggregate larger than that gets a CTA of its own).
+// Staging capacities of a set of CTA row ranges; staging is switched off for
+// the level when the largest slice would not fit comfortably in shared memory.
+static Stage make_stage(const std::vector<int>& rp, const std::vector<int>& cr, int* err) {
+  Stage sg;
+  sg.err = err;
+  for (size_t c = 0; c + 1 < cr.size(); ++c) {
+    int r0 = cr[c], r1 = cr[c + 1], j0 = rp[r0], j1 = rp[r1];
+    sg.rows_max = std::max(sg.rows_max, r1 - r0);
+    sg.span4 = std::max(sg.span4, ((j1 + 3) & ~3) - (j0 & ~3));
+    sg.span8 = std::max(sg.span8, ((j1 + 1) & ~1) - (j0 & ~1));
+  }
+  sg.enabled = 1;
+  if (stage_bytes(sg, 2, 1) > 96 * 1024) sg.enabled = 0;
+  return sg;
+}
+
+// Non-zeros per CTA of the row-parallel kernels: more columns, fewer rows.
+static long long target_nnz(int K) { return K == 1 ? 4096 : (K <= 4 ? 2048 : 1024); }
+
+static RPart make_rpart(Arena& ar, const Level& L, long long target, const std::vector<int>& sys_rows,
+                        int* err) {
+  const std::vector<int>& rp = L.h_rowptr;
+  std::vector<int> cr{0}, sys_cta{0}, grp{0}, sys_grp{0};
+  for (size_t s = 0; s + 1 < sys_rows.size(); ++s) {
+    int r = sys_rows[s];
+    const int end = sys_rows[s + 1];
+    while (r < end) {
+      const int start = r;
+      const long long base = rp[r];
+      ++r;
+      while (r < end && rp[r + 1] - base <= target && r - start < 1024) ++r;
+      cr.push_back(r);
+    }
+    const int c1 = (int)cr.size() - 1;
+    for (int c = sys_cta.back(); c < c1; c += 64) grp.push_back(std::min(c + 64, c1));
+    sys_cta.push_back(c1);
+    sys_grp.push_back((int)grp.size() - 1);
+  }
+  RPart p;
+  p.ncta = (int)cr.size() - 1;
+  p.ngroups = (int)grp.size() - 1;
+  auto up = [&](const std::vector<int>& v) {
+    int* d = ar.alloc<int>(v.size());
+    AMG_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return d;
+  };
+  p.cta_row = up(cr);
+  p.grp_cta = up(grp);
+  p.sys_grp = up(sys_grp);
+  p.sys_cta = up(sys_cta);
+  p.sg = make_stage(rp, cr, err);
+  return p;
+}
+
+static TPart make_tpart(Arena& ar, const Transfer& T, const Level& F, int K, int* err) {
+  int target = K <= 2 ? 256 : (K <= 8 ? 128 : 64);
+  std::vector<int> ca{0};
+  int rows = 0;
+  for (int a = 0; a < T.nagg; ++a) {
+    int na = T.h_row_start[a + 1] - T.h_row_start[a];
+    if (rows > 0 && rows + na > target) {
+      ca.push_back(a);
+      rows = 0;
+    }
+    rows += na;
+  }
+  ca.push_back(T.nagg);
+  TPart tp;
+  tp.ncta = (int)ca.size() - 1;
+  for (int c = 0; c < tp.ncta; ++c) {
+    int a0 = ca[c], a1 = ca[c + 1];
+    tp.rows_max = std::max(tp.rows_max, T.h_row_start[a1] - T.h_row_start[a0]);
+    tp.p_max = std::max(tp.p_max, (int)(T.h_blk_start[a1] - T.h_blk_start[a0]));
+    tp.a_max = std::max(tp.a_max, a1 - a0);
+    tp.c_max = std::max(tp.c_max, T.h_coarse_start[a1] - T.h_coarse_start[a0]);
+  }
+  tp.cta_agg = ar.alloc<int>(ca.size());
+  AMG_CUDA(cudaMemcpy(tp.cta_agg, ca.data(), ca.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<int> cr(ca.size());
+  for (size_t c = 0; c < ca.size(); ++c) cr[c] = T.h_row_start[ca[c]];
+  tp.sg = make_stage(F.h_rowptr, cr, err);
+  return tp;
+}
+
 static int round_k(int nrhs) {
   int K = 1;
   while (K < nrhs) K <<= 1;
   return K;
 }
 
-static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post) {
-  long long key = ((long long)K << 32) | ((long long)prec << 16) | ((long long)pre << 8) | post;
+// ------------------------------------------------------------ autotuner --
+// Per level: the CTA size (non-zeros per CTA) and the lanes per row of the
+// row-parallel kernels, chosen by timing the level's l1-Jacobi sweep with
+// every candidate on the workspace's own buffers (their contents do not
+// matter for timing).  The chosen layout serves every kernel of the level.
+static const long long kTargets[] = {512, 1024, 2048, 4096, 8192};
+
+template <typename TC>
+static std::vector<int> nzl_candidates(int K) {
+  std::vector<int> v;
+  int mx = max_nzl<TC>(K);
+  for (int n : {1, 2, 4, 8, 16, 32})
+    if (n <= mx && (K > 1 ? n <= 8 : n >= 2)) v.push_back(n);
+  return v;
+}
+
+template <typename TC>
+static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys) {
+  const Level& L = P.lev[k];
+  const int K = W.K;
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  long long bt = target_nnz(K);
+  int bn = W.nzl[k];
+  {
+    Arena tmp;
+    for (long long t : kTargets) {
+      RPart rp = make_rpart(tmp, L, t, sys, W.err);
+      if (t > kTargets[0] && rp.ncta < 152) break;  // fewer CTAs than SMs: stop growing
+      for (int n : nzl_candidates<TC>(K)) {
+        TC* f = static_cast<TC*>(W.f[k]);
+        TC* u = static_cast<TC*>(W.u[k]);
+        TC* v = static_cast<TC*>(W.v[k]);
+        launch_smooth<TC>(K, n, L, rp, f, u, v, W.zero_flag, 0);
+        AMG_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 3; ++r) launch_smooth<TC>(K, n, L, rp, f, u, v, W.zero_flag, 0);
+        AMG_CUDA(cudaEventRecord(e1, 0));
+        AMG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bt = t;
+          bn = n;
+        }
+      }
+    }
+    AMG_CUDA(cudaDeviceSynchronize());
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  W.rp[k] = make_rpart(W.ar, L, bt, sys, W.err);
+  W.nzl[k] = bn;
+}
+
+static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
+
+// Lanes per row of the outer q = A p on the chosen level-0 layout (its CG
+// state is reset by the start of every solve, so timing runs are harmless).
+static void tune_q(Plan& P, Workspace& W) {
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bn = W.nzl_q;
+  std::vector<int> cand = W.split ? nzl_candidates<float>(W.K) : nzl_candidates<double>(W.K);
+  for (int n : cand) {
+    W.nzl_q = n;
+    launch_cg_q(W, P.lev[0], 0);
+    AMG_CUDA(cudaEventRecord(e0, 0));
+    for (int r = 0; r < 3; ++r) launch_cg_q(W, P.lev[0], 0);
+    AMG_CUDA(cudaEventRecord(e1, 0));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      bn = n;
+    }
+  }
+  W.nzl_q = bn;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false) {
+  long long key = ((long long)split << 40) | ((long long)K << 32) | ((long long)prec << 16) |
+                  ((long long)pre << 8) | post;
   auto it = P.ws.find(key);
   if (it != P.ws.end()) return *it->second;
   auto W = std::make_shared<Workspace>();
@@ -295,7 +716,12 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post) {
   size_t n0k = (size_t)W->n0 * K;
   W->x = ar.alloc<double>(n0k);
   W->r = ar.alloc<double>(n0k);
-  W->p = ar.alloc<double>(n0k);
+  W->split = split;
+  if (split) {
+    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->pl, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
+  } else {
+    W->p = ar.alloc<double>(n0k);
+  }
   W->q = ar.alloc<double>(n0k);
   W->z = ar.alloc<double>(n0k);
   W->b = ar.alloc<double>(n0k);
@@ -305,16 +731,43 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post) {
   W->v.resize(P.L);
   for (int k = 0; k < P.L; ++k) {
     size_t nk = (size_t)P.lev[k].n * K;
-    W->f[k] = (k == 0 && prec == 64) ? (void*)W->r : ar.raw(nk * es);
+    if (k == 0 && prec == 64) W->f[k] = W->r;
+    else if (k == 0 && split) W->f[k] = W->rh;   // r_hi is the float32 level-0 right-hand side
+    else W->f[k] = ar.raw(nk * es);
     W->u[k] = ar.raw(nk * es);
     W->v[k] = ar.raw(nk * es);
   }
-  int ncta0 = P.lev[0].ncta;
+  W->err = ar.alloc<int>(1);
+  AMG_CUDA(cudaMemset(W->err, 0, sizeof(int)));
+  W->zero_flag = ar.alloc<int>(1);
+  AMG_CUDA(cudaMemset(W->zero_flag, 0, sizeof(int)));
+  W->nzl.resize(P.L);
+  for (int k = 0; k < P.L; ++k) {
+    std::vector<int> sys = (k == 0) ? P.h_sys_row : std::vector<int>{0, P.lev[k].n};
+    W->rp.push_back(make_rpart(ar, P.lev[k], target_nnz(K), sys, W->err));
+    W->nzl[k] = prec == 64 ? pick_nzl<double>(P.lev[k], K) : pick_nzl<float>(P.lev[k], K);
+  }
+  W->nzl_q = split ? pick_nzl<float>(P.lev[0], K) : pick_nzl<double>(P.lev[0], K);
+  if (autotune) {
+    for (int k = 0; k + 1 < P.L; ++k) {  // smoothed levels (the coarsest has no smoother)
+      std::vector<int> sys = (k == 0) ? P.h_sys_row : std::vector<int>{0, P.lev[k].n};
+      if (prec == 64) tune_level<double>(P, *W, k, sys);
+      else tune_level<float>(P, *W, k, sys);
+    }
+  }
+  const RPart& r0p = W->rp[0];
   int nv = P.nsys * K;
   KState& ks = W->ks;
-  ks.partial = ar.alloc<double>((size_t)ncta0 * 2 * K);
-  ks.counter = ar.alloc<unsigned>(8);
-  AMG_CUDA(cudaMemset(ks.counter, 0, 8 * sizeof(unsigned)));
+  ks.partial = ar.alloc<double>((size_t)r0p.ncta * 2 * K);
+  ks.gpartial = ar.alloc<double>((size_t)r0p.ngroups * 2 * K);
+  ks.counter = ar.alloc<unsigned>(RED_KINDS);
+  AMG_CUDA(cudaMemset(ks.counter, 0, RED_KINDS * sizeof(unsigned)));
+  ks.gcount = ar.alloc<unsigned>((size_t)RED_KINDS * r0p.ngroups);
+  AMG_CUDA(cudaMemset(ks.gcount, 0, (size_t)RED_KINDS * r0p.ngroups * sizeof(unsigned)));
+  ks.grp_cta = r0p.grp_cta;
+  ks.sys_grp = r0p.sys_grp;
+  ks.ngroups = r0p.ngroups;
+  ks.sg = r0p.sg;
   ks.rho = ar.alloc<double>(nv);
   ks.alpha = ar.alloc<double>(nv);
   ks.beta = ar.alloc<double>(nv);
@@ -326,17 +779,14 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post) {
   ks.active = ar.alloc<int>(P.nsys);
   ks.done = ar.alloc<int>(1);
   ks.iter = ar.alloc<int>(1);
-  ks.sys_cta = P.sys_cta;
+  ks.sys_cta = r0p.sys_cta;
   ks.nsys = P.nsys;
-  W->zero_flag = ar.alloc<int>(1);
-  AMG_CUDA(cudaMemset(W->zero_flag, 0, sizeof(int)));
   AMG_CUDA(cudaMemset(ks.done, 0, sizeof(int)));
   AMG_CUDA(cudaMallocHost(&W->h_done, sizeof(int)));
   AMG_CUDA(cudaMallocHost(&W->h_iter, sizeof(int)));
-  W->nzl.resize(P.L);
-  for (int k = 0; k < P.L; ++k)
-    W->nzl[k] = prec == 64 ? pick_nzl<double>(P.lev[k], K) : pick_nzl<float>(P.lev[k], K);
+  for (int k = 0; k + 1 < P.L; ++k) W->tp.push_back(make_tpart(ar, P.tr[k], P.lev[k], K, W->err));
   AMG_CUDA(cudaDeviceSynchronize());
+  if (autotune) tune_q(P, *W);
   P.ws[key] = W;
   return *W;
 }
@@ -405,14 +855,14 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   auto F = [&](int k) { return static_cast<TC*>(W.f[k]); };
   for (int k = 0; k + 1 < L; ++k) {
     for (int s = 1; s < W.pre; ++s) {
-      launch_smooth<TC>(K, W.nzl[k], P.lev[k], F(k), cur[k], oth[k], done, st);
+      launch_smooth<TC>(K, W.nzl[k], P.lev[k], W.rp[k], F(k), cur[k], oth[k], done, st);
       std::swap(cur[k], oth[k]);
     }
     bool smooth_next = (k + 1 < L - 1);
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_RESTRICT_L0 : -1, st, pool);
-      launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], P.lev[k + 1], smooth_next, F(k), cur[k], F(k + 1),
-                          cur[k + 1], done, st);
+      launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], W.tp[k], P.lev[k + 1], smooth_next, F(k), cur[k],
+                          F(k + 1), cur[k + 1], done, st);
     }
   }
   launch_coarse<TC>(K, P.co, F(L - 1), cur[L - 1], done, st);
@@ -420,26 +870,47 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   for (int k = L - 2; k >= 0; --k) {
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_PROLONG_L0 : -1, st, pool);
-      launch_prolong<TC>(K, P.tr[k], res, cur[k], done, st);
+      launch_prolong<TC>(K, P.tr[k], W.tp[k], res, cur[k], done, st);
     }
     int sweeps = (k == 0) ? W.post - 1 : W.post;
     for (int s = 0; s < sweeps; ++s) {
-      launch_smooth<TC>(K, W.nzl[k], P.lev[k], F(k), cur[k], oth[k], done, st);
+      launch_smooth<TC>(K, W.nzl[k], P.lev[k], W.rp[k], F(k), cur[k], oth[k], done, st);
       std::swap(cur[k], oth[k]);
     }
     res = cur[k];
   }
   TimedLaunch tl(h, AMG_KERNEL_SMOOTH_L0, st, pool);
-  launch_post0<TC>(K, W.nzl[0], P.lev[0], F(0), cur[0], W.r, W.z, ks, mode, st);
+  launch_post0<TC>(K, W.nzl[0], P.lev[0], W.rp[0], F(0), cur[0], W.r, W.split ? W.rl : nullptr,
+                   reinterpret_cast<TC*>(W.z), ks, mode, st);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
+  if (W.split) {
+    dispatch_k(W.K, [&](auto kc) {
+      constexpr int KK = decltype(kc)::value;
+      dispatch_nzl(W.K, W.nzl_q, [&](auto nc) {
+        constexpr int NZ = decltype(nc)::value;
+        if constexpr (VT<float, KK>::CL * NZ <= 32) {
+          auto kern = k_cg_q_df<KK, NZ>;
+          size_t smem = stage_bytes(W.rp[0].sg, 2, 0);
+          ensure_smem(kern, smem);
+          kern<<<W.rp[0].ncta, BS, smem, st>>>(W.rp[0].cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.pl,
+                                               W.qh, W.ql, W.ks);
+        }
+      });
+    });
+    AMG_LAUNCH_CHECK();
+    return;
+  }
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    dispatch_nzl(W.K, pick_nzl<double>(L, W.K), [&](auto nc) {
+    dispatch_nzl(W.K, W.nzl_q, [&](auto nc) {
       constexpr int NZ = decltype(nc)::value;
       if constexpr (VT<double, KK>::CL * NZ <= 32) {
-        k_cg_q<KK, NZ><<<L.ncta, BS, 0, st>>>(L.cta_row, L.rowptr, L.col, L.val64, W.p, W.q, W.ks);
+        auto kern = k_cg_q<KK, NZ>;
+        size_t smem = stage_bytes(W.rp[0].sg, 0, 1);
+        ensure_smem(kern, smem);
+        kern<<<W.rp[0].ncta, BS, smem, st>>>(W.rp[0].cta_row, L.rowptr, L.col, L.val64, W.p, W.q, W.ks);
       }
     });
   });
@@ -449,28 +920,60 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
 static void launch_cg_init(Workspace& W, const Level& L, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    dispatch_nzl(W.K, pick_nzl<double>(L, W.K), [&](auto nc) {
+    dispatch_nzl(W.K, W.split ? pick_nzl<double>(L, W.K) : W.nzl_q, [&](auto nc) {
       constexpr int NZ = decltype(nc)::value;
       if constexpr (VT<double, KK>::CL * NZ <= 32) {
-        k_cg_init<KK, NZ><<<L.ncta, BS, 0, st>>>(L.cta_row, L.rowptr, L.col, L.val64, W.b, W.x, W.r, W.ks);
+        auto kern = k_cg_init<KK, NZ>;
+        size_t smem = stage_bytes(W.rp[0].sg, 0, 1);
+        ensure_smem(kern, smem);
+        kern<<<W.rp[0].ncta, BS, smem, st>>>(W.rp[0].cta_row, L.rowptr, L.col, L.val64, W.b, W.x, W.r, W.ks);
       }
     });
   });
   AMG_LAUNCH_CHECK();
 }
 
-static void launch_cg_p(Workspace& W, const Level& L, cudaStream_t st) {
+// z holds float32 values when the cycle runs in float32 (and the hierarchy
+// has a cycle at all); the one-level solve writes float64.
+static bool z_is_f32(const Plan& P, const Workspace& W) { return W.prec == 32 && P.L > 1; }
+
+static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    k_cg_p<KK><<<L.ncta, BS, 0, st>>>(L.cta_row, W.z, W.p, W.ks);
+    if (W.split)
+      k_cg_p_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph,
+                                                 W.pl, W.ks, first);
+    else if (z_is_f32(P, W))
+      k_cg_p<KK, float><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.p,
+                                                     W.ks, first);
+    else
+      k_cg_p<KK, double><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.z, W.p, W.ks, first);
   });
+  AMG_LAUNCH_CHECK();
+}
+
+static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st) {
+  dispatch_k(W.K, [&](auto kc) {
+    constexpr int KK = decltype(kc)::value;
+    k_cg_update_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.xh, W.xl, W.rh, W.rl, W.ph, W.pl, W.qh, W.ql,
+                                              L.dinv32, static_cast<float*>(W.u[0]), W.ks);
+  });
+  AMG_LAUNCH_CHECK();
+}
+
+static void launch_pair(bool split_dir, long long n, const double* v, float* h, float* l, double* out,
+                        const int* done, cudaStream_t st) {
+  unsigned grid = (unsigned)((n + 255) / 256);
+  (void)done;
+  if (split_dir) k_split_pair<<<grid, 256, 0, st>>>(n, v, h, l);
+  else k_join_pair<<<grid, 256, 0, st>>>(n, h, l, out);
   AMG_LAUNCH_CHECK();
 }
 
 static void launch_rz(Workspace& W, const Level& L, int mode, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    k_rz<KK><<<L.ncta, BS, 0, st>>>(L.cta_row, W.r, W.z, W.ks, mode);
+    k_rz<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.r, W.z, W.ks, mode);
   });
   AMG_LAUNCH_CHECK();
 }
@@ -483,11 +986,17 @@ static void enqueue_start(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     enqueue_cycle<TC>(h, P, W, st, 0, W.ks.done, W.ks, nullptr);
     launch_rz(W, L0, 0, st);
   } else {
-    TC* f0 = (W.prec == 64) ? nullptr : static_cast<TC*>(W.f[0]);
-    launch_presmooth0<TC>(W.K, L0, W.r, static_cast<TC*>(W.u[0]), f0, W.ks.done, st);
+    if (W.split) {
+      // x and r enter the double-float pairs; r_hi is the cycle's f0
+      long long nk = (long long)W.n0 * W.K;
+      launch_pair(true, nk, W.r, W.rh, W.rl, nullptr, W.ks.done, st);
+      launch_pair(true, nk, W.x, W.xh, W.xl, nullptr, W.ks.done, st);
+    }
+    TC* f0 = (W.prec == 64 || W.split) ? nullptr : static_cast<TC*>(W.f[0]);
+    launch_presmooth0<TC>(W.K, L0, W.rp[0], W.r, static_cast<TC*>(W.u[0]), f0, W.ks.done, st);
     enqueue_cycle<TC>(h, P, W, st, 0, W.ks.done, W.ks, nullptr);
   }
-  launch_cg_p(W, L0, st);
+  launch_cg_p(P, W, L0, 1, st);
 }
 
 template <typename TC>
@@ -502,11 +1011,12 @@ static void enqueue_iteration(amg_hierarchy* h, Plan& P, Workspace& W, cudaStrea
   {
     TimedLaunch tl(h, AMG_KERNEL_CG_UPDATE, st, pool);
     TC* u0 = P.L == 1 ? nullptr : static_cast<TC*>(W.u[0]);
-    launch_update<TC>(W.K, L0, W.x, W.r, W.p, W.q, u0, f0, W.ks, st);
+    if (W.split) launch_update_df(W, L0, st);
+    else launch_update<TC>(W.K, L0, W.rp[0], W.x, W.r, W.p, W.q, u0, f0, W.ks, st);
   }
   enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
   if (P.L == 1) launch_rz(W, L0, 1, st);
-  launch_cg_p(W, L0, st);
+  launch_cg_p(P, W, L0, 0, st);
 }
 
 // ----------------------------------------------------------------- PCG --
@@ -655,7 +1165,8 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   AMG_REQUIRE(o.pre >= 1 && o.post >= 1 && o.pre <= 16 && o.post <= 16, "pre and post sweeps must be in [1, 16]");
   AMG_REQUIRE(o.maxit >= 1 && o.rtol >= 0, "maxit must be >= 1 and rtol >= 0");
   const int K = round_k(maxr);
-  Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post);
+  const bool split = o.cycle_precision == 32 && !o.outer_fp64 && P.L > 1;
+  Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, split, o.autotune != 0);
   W.ks.rtol = o.rtol;
   W.ks.maxit = o.maxit;
   StreamJoin sj(owner, user);
@@ -665,6 +1176,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   stage_inputs(P, W, rq, st);
   if (o.cycle_precision == 64) pcg_loop<double>(owner, P, W, o, st);
   else pcg_loop<float>(owner, P, W, o, st);
+  if (W.split) launch_pair(false, (long long)W.n0 * K, nullptr, W.xh, W.xl, W.x, nullptr, st);
   stage_outputs(P, W, rq, W.x, st);
   // results
   int nv = P.nsys * K;
@@ -675,7 +1187,13 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   AMG_CUDA(cudaMemcpyAsync(status.data(), W.ks.status, nv * 4, cudaMemcpyDeviceToHost, st));
   AMG_CUDA(cudaMemcpyAsync(rn.data(), W.ks.rnorm, nv * 8, cudaMemcpyDeviceToHost, st));
   AMG_CUDA(cudaMemcpyAsync(bn.data(), W.ks.bnorm, nv * 8, cudaMemcpyDeviceToHost, st));
+  int werr = 0;
+  AMG_CUDA(cudaMemcpyAsync(&werr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   sj.finish();
+  if (werr) {
+    AMG_CUDA(cudaMemset(W.err, 0, sizeof(int)));
+    throw Error(AMG_ERR_TIMEOUT, "a bounded wait for a shared-memory staging copy gave up");
+  }
   amg_status res = AMG_OK;
   int idx = 0;
   for (int s = 0; s < rq.nsys; ++s) {
@@ -720,14 +1238,21 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
   if (P.L == 1) {
     launch_coarse<double>(K, P.co, W.r, W.z, W.zero_flag, st);
   } else if (o.cycle_precision == 64) {
-    launch_presmooth0<double>(K, P.lev[0], W.r, static_cast<double*>(W.u[0]), nullptr, W.zero_flag, st);
+    launch_presmooth0<double>(K, P.lev[0], W.rp[0], W.r, static_cast<double*>(W.u[0]), nullptr, W.zero_flag, st);
     enqueue_cycle<double>(nullptr, P, W, st, 2, W.zero_flag, ks, nullptr);
   } else {
-    launch_presmooth0<float>(K, P.lev[0], W.r, static_cast<float*>(W.u[0]), static_cast<float*>(W.f[0]),
+    launch_presmooth0<float>(K, P.lev[0], W.rp[0], W.r, static_cast<float*>(W.u[0]), static_cast<float*>(W.f[0]),
                              W.zero_flag, st);
     enqueue_cycle<float>(nullptr, P, W, st, 2, W.zero_flag, ks, nullptr);
   }
-  stage_outputs(P, W, rq, W.z, st);
+  double* zout = W.z;
+  if (z_is_f32(P, W)) {
+    long long nz = (long long)W.n0 * K;
+    k_f32_to_f64<<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(nz, reinterpret_cast<const float*>(W.z), W.q);
+    AMG_LAUNCH_CHECK();
+    zout = W.q;
+  }
+  stage_outputs(P, W, rq, zout, st);
   sj.finish();
 }
 
