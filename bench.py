@@ -52,15 +52,19 @@ def parse():
 
 
 # ------------------------------------------------------------------ dist --
-def dist_init():
+def dist_init(backend="nccl"):
+    """Join the process group of a torchrun launch (one replica per GPU)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -75,9 +79,27 @@ def max_over_ranks(v, ws):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rhs_block(P, batch, rank):
+    """The right-hand sides of one replica: seeded uniform[-1, 1], distinct
+    per rank; rank 0's first column is the workload's own RHS."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(1002 + 7919 * rank))
+    B = rng.uniform(-1.0, 1.0, size=(P.n, batch))
+    if rank == 0:
+        B[:, 0] = P.B[:, 0]
+    return B
+
+
+def whole_job_ms_per_rhs(max_elapsed_ms, steps, batch, ws):
+    """Weak scaling: every rank solves ``batch`` RHS per step; the job's time
+    per step is the slowest rank's."""
+    return max_elapsed_ms / steps / (batch * ws)
 
 
 # ---------------------------------------------------------------- clocks --
@@ -257,10 +279,7 @@ def main():
     dev = torch.device("cuda", local)
     t_gen = time.time()
     P = inputs.anisotropic(N=args.grid, nrhs=1)
-    rng = np.random.Generator(np.random.PCG64(1002 + 7919 * rank))
-    B = rng.uniform(-1.0, 1.0, size=(P.n, args.batch))
-    if rank == 0:
-        B[:, 0] = P.B[:, 0]
+    B = rhs_block(P, args.batch, rank)
     t_gen = time.time() - t_gen
 
     A = P.A
@@ -322,8 +341,7 @@ def main():
     elapsed = e0.elapsed_time(e1)
     elapsed = max_over_ranks(elapsed, ws)
     per_step = elapsed / args.steps
-    # whole job: ws * batch RHS per step in the slowest rank's time
-    value_job = per_step / (args.batch * ws)
+    value_job = whole_job_ms_per_rhs(elapsed, args.steps, args.batch, ws)
     print(f"[bench] timed {args.steps} steps: {per_step:.1f} ms/step, iters {iters[0][:4]}..., "
           f"kernel {rk}: {kms:.2f} ms over {kn} launches, gpu launches {launches}", file=sys.stderr, flush=True)
     if shares is not None:

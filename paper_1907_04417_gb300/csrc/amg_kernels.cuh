@@ -284,6 +284,25 @@ __device__ __forceinline__ void df_mac(float ah, float al, float xh, float xl, f
   e += sl + pl;
   df_fast_two_sum(s, e, sh, sl);
 }
+// Accumulating form: (sh, sl) += (ah, al) * (xh, xl) with the low word left
+// unnormalised (the product error, the cross terms and the two-sum error all
+// go to sl); df_norm once after the last term.
+__device__ __forceinline__ void df_acc(float ah, float al, float xh, float xl, float& sh, float& sl) {
+  float p = ah * xh;
+  float e = fmaf(ah, xh, -p);
+  e = fmaf(ah, xl, fmaf(al, xh, e));
+  float s = sh + p;
+  float v = s - sh;
+  float t = (sh - (s - v)) + (p - v);
+  sh = s;
+  sl += t + e;
+}
+__device__ __forceinline__ void df_norm(float& sh, float& sl) {
+  float s, e;
+  df_fast_two_sum(sh, sl, s, e);
+  sh = s;
+  sl = e;
+}
 // (sh, sl) += (oh, ol)
 __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol) {
   float s, e;
@@ -569,39 +588,34 @@ __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg,
 }
 
 // Coarsest level: u = A_c^{-1} f with the float64 inverse of each diagonal
-// block (one warp per row, float64 accumulation).
+// block; one thread per (row, column) with float64 accumulation, spread over
+// many small CTAs (the float64 pipes of GB300 are narrow).
+constexpr int COARSE_BS = 64;
 template <typename TC, int K>
-__global__ void __launch_bounds__(BS) k_coarse(int n, int nblk, const int* __restrict__ blk_off,
-                                               const long long* __restrict__ inv_off,
-                                               const double* __restrict__ inv, const TC* __restrict__ f,
-                                               TC* __restrict__ u, const int* __restrict__ done) {
+__global__ void __launch_bounds__(COARSE_BS) k_coarse(int n, int nblk, const int* __restrict__ blk_off,
+                                                      const long long* __restrict__ inv_off,
+                                                      const double* __restrict__ inv, const TC* __restrict__ f,
+                                                      TC* __restrict__ u, const int* __restrict__ done) {
   if (*done) return;
-  const int lane = threadIdx.x & 31;
-  const int row = (blockIdx.x * BS + threadIdx.x) >> 5;
-  if (row >= n) return;
+  const long long t = (long long)blockIdx.x * COARSE_BS + threadIdx.x;
+  if (t >= (long long)n * K) return;
+  const int row = (int)(t / K), c = (int)(t % K);
   int lo = 0, hi = nblk - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (__ldg(blk_off + mid) <= row) lo = mid; else hi = mid - 1;
   }
-  const int b0 = blk_off[lo], nb = blk_off[lo + 1] - b0;
-  const double* Ar = inv + inv_off[lo] + (size_t)(row - b0) * nb;
-  double acc[K];
-#pragma unroll
-  for (int c = 0; c < K; ++c) acc[c] = 0.0;
-  for (int j = lane; j < nb; j += 32) {
-    double a = __ldg(Ar + j);
-    const TC* fj = f + (size_t)(b0 + j) * K;
-#pragma unroll
-    for (int c = 0; c < K; ++c) acc[c] = fma(a, (double)fj[c], acc[c]);
+  const int b0 = __ldg(blk_off + lo), nb = __ldg(blk_off + lo + 1) - b0;
+  const double* Ar = inv + __ldg(inv_off + lo) + (size_t)(row - b0) * nb;
+  const TC* fc = f + (size_t)b0 * K + c;
+  double s0 = 0.0, s1 = 0.0;
+  int j = 0;
+  for (; j + 1 < nb; j += 2) {
+    s0 = fma(__ldg(Ar + j), (double)__ldg(fc + (size_t)j * K), s0);
+    s1 = fma(__ldg(Ar + j + 1), (double)__ldg(fc + (size_t)(j + 1) * K), s1);
   }
-#pragma unroll
-  for (int c = 0; c < K; ++c) {
-    double s = acc[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-    if (lane == c % 32) u[(size_t)row * K + c] = (TC)s;
-  }
+  if (j < nb) s0 = fma(__ldg(Ar + j), (double)__ldg(fc + (size_t)j * K), s0);
+  u[(size_t)row * K + c] = (TC)(s0 + s1);
 }
 
 // ----------------------------------------------------- fused CG kernels --

@@ -174,10 +174,11 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   template <>                                                                                          \
   void launch_coarse<TC>(int K, const Coarsest& C, const TC* f, TC* u, const int* done,                \
                          cudaStream_t st) {                                                            \
-    int grid = (C.n * 32 + BS - 1) / BS;                                                               \
+    int grid = (int)(((long long)C.n * K + COARSE_BS - 1) / COARSE_BS);                                 \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
-      k_coarse<TC, KK><<<grid, BS, 0, st>>>(C.n, C.nblk, C.blk_off, C.inv_off, C.inv, f, u, done);    \
+      k_coarse<TC, KK><<<grid, COARSE_BS, 0, st>>>(C.n, C.nblk, C.blk_off, C.inv_off, C.inv, f, u,     \
+                                                   done);                                              \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \

@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
         ldv<float, CPT>(pl + (size_t)c1 * K + cl * CPT, xl1);
 #pragma unroll
         for (int t = 0; t < CPT; ++t) {
-          df_mac(ah0, al0, xh0[t], xl0[t], sh[t], sl[t]);
-          df_mac(ah1, al1, xh1[t], xl1[t], sh[t], sl[t]);
+          df_acc(ah0, al0, xh0[t], xl0[t], sh[t], sl[t]);
+          df_acc(ah1, al1, xh1[t], xl1[t], sh[t], sl[t]);
         }
       }
       for (; j < j1; j += NZL) {
@@ -114,8 +114,10 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
         ldv<float, CPT>(ph + (size_t)c * K + cl * CPT, xh);
         ldv<float, CPT>(pl + (size_t)c * K + cl * CPT, xl);
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) df_mac(ah, al, xh[t], xl[t], sh[t], sl[t]);
+        for (int t = 0; t < CPT; ++t) df_acc(ah, al, xh[t], xl[t], sh[t], sl[t]);
       }
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) df_norm(sh[t], sl[t]);
     }
     if constexpr (NZL > 1) {
 #pragma unroll
@@ -286,12 +288,11 @@ __global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, co
 
 __device__ __forceinline__ void split2(double v, float& h, float& l) { df_split(v, h, l); }
 
-// x += alpha p, r -= alpha q, ||r||^2; u0 = D^{-1} r_hi (first pre-sweep).
+// r -= alpha q, ||r||^2; u0 = D^{-1} r_hi (first pre-sweep).  (x is
+// advanced by k_cg_p_df, which streams p anyway.)
 template <int K>
-__global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta_row, float* __restrict__ xh,
-                                                     float* __restrict__ xl, float* __restrict__ rh,
-                                                     float* __restrict__ rl, const float* __restrict__ ph,
-                                                     const float* __restrict__ pl, const float* __restrict__ qh,
+__global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta_row, float* __restrict__ rh,
+                                                     float* __restrict__ rl, const float* __restrict__ qh,
                                                      const float* __restrict__ ql, const float* __restrict__ dinv,
                                                      float* __restrict__ u0, KState ks) {
   if (*ks.done) return;
@@ -305,29 +306,22 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
   float ah[CPT], al[CPT], dh[CPT], dl[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
-    split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+    split2(-ks.alpha[s * K + cfirst + t], ah[t], al[t]);
     dh[t] = dl[t] = 0.f;
   }
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
-    float xa[CPT], xb[CPT], ra[CPT], rb[CPT], pa[CPT], pb[CPT], qa[CPT], qb[CPT], uo[CPT];
-    ldp<float, CPT>(xh + e, xa);
-    ldp<float, CPT>(xl + e, xb);
+    float ra[CPT], rb[CPT], qa[CPT], qb[CPT], uo[CPT];
     ldp<float, CPT>(rh + e, ra);
     ldp<float, CPT>(rl + e, rb);
-    ldv<float, CPT>(ph + e, pa);
-    ldv<float, CPT>(pl + e, pb);
     ldv<float, CPT>(qh + e, qa);
     ldv<float, CPT>(ql + e, qb);
     float di = __ldg(dinv + e / K);
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
-      df_mac(ah[t], al[t], pa[t], pb[t], xa[t], xb[t]);
-      df_mac(-ah[t], -al[t], qa[t], qb[t], ra[t], rb[t]);
-      df_mac(ra[t], rb[t], ra[t], rb[t], dh[t], dl[t]);
+      df_mac(ah[t], al[t], qa[t], qb[t], ra[t], rb[t]);
+      df_acc(ra[t], rb[t], ra[t], rb[t], dh[t], dl[t]);
       uo[t] = di * ra[t];
     }
-    stv<float, CPT>(xh + e, xa);
-    stv<float, CPT>(xl + e, xb);
     stv<float, CPT>(rh + e, ra);
     stv<float, CPT>(rl + e, rb);
     stv<float, CPT>(u0 + e, uo);
@@ -340,10 +334,14 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
   finish_update<K>(ks, sm, tot);
 }
 
-// p = z + beta p on the double-float pair (first: p = z).
+// x += alpha p (with the alpha of this iteration), then p = z + beta p, on
+// double-float pairs; ``first`` starts the recurrence (p = z, x untouched).
+// After the last iteration k_cg_x_df applies the final alpha p, which this
+// kernel skips once every column has stopped.
 template <int K>
 __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
-                                                float* __restrict__ ph, float* __restrict__ pl, KState ks,
+                                                float* __restrict__ ph, float* __restrict__ pl,
+                                                float* __restrict__ xh, float* __restrict__ xl, KState ks,
                                                 int first) {
   if (*ks.done) return;
   constexpr int CPT = VT<float, K>::CPT;
@@ -351,9 +349,12 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
   const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
   const int cfirst = (int)((threadIdx.x * CPT) % K);
   const int s = cta_system(ks.sys_cta, ks.nsys);
-  float bh[CPT], bl[CPT];
+  float bh[CPT], bl[CPT], ah[CPT], al[CPT];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) split2(ks.beta[s * K + cfirst + t], bh[t], bl[t]);
+  for (int t = 0; t < CPT; ++t) {
+    split2(ks.beta[s * K + cfirst + t], bh[t], bl[t]);
+    split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+  }
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
     float zv[CPT], pa[CPT], pb[CPT];
     ldv<float, CPT>(z + e, zv);
@@ -364,18 +365,51 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
         pb[t] = 0.f;
       }
     } else {
+      float xa[CPT], xb[CPT];
       ldp<float, CPT>(ph + e, pa);
       ldp<float, CPT>(pl + e, pb);
+      ldp<float, CPT>(xh + e, xa);
+      ldp<float, CPT>(xl + e, xb);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
+        df_mac(ah[t], al[t], pa[t], pb[t], xa[t], xb[t]);
         float sh = zv[t], sl = 0.f;
         df_mac(bh[t], bl[t], pa[t], pb[t], sh, sl);
         pa[t] = sh;
         pb[t] = sl;
       }
+      stv<float, CPT>(xh + e, xa);
+      stv<float, CPT>(xl + e, xb);
     }
     stv<float, CPT>(ph + e, pa);
     stv<float, CPT>(pl + e, pb);
+  }
+}
+
+// x += alpha p once after the loop (the step of the last iteration; the
+// alpha of columns that stopped earlier is already zero).
+template <int K>
+__global__ void __launch_bounds__(BS) k_cg_x_df(const int* __restrict__ cta_row, const float* __restrict__ ph,
+                                                const float* __restrict__ pl, float* __restrict__ xh,
+                                                float* __restrict__ xl, KState ks) {
+  constexpr int CPT = VT<float, K>::CPT;
+  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
+  const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
+  const int cfirst = (int)((threadIdx.x * CPT) % K);
+  const int s = cta_system(ks.sys_cta, ks.nsys);
+  float ah[CPT], al[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+  for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
+    float pa[CPT], pb[CPT], xa[CPT], xb[CPT];
+    ldv<float, CPT>(ph + e, pa);
+    ldv<float, CPT>(pl + e, pb);
+    ldp<float, CPT>(xh + e, xa);
+    ldp<float, CPT>(xl + e, xb);
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) df_mac(ah[t], al[t], pa[t], pb[t], xa[t], xb[t]);
+    stv<float, CPT>(xh + e, xa);
+    stv<float, CPT>(xl + e, xb);
   }
 }
 
@@ -942,7 +976,7 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
     constexpr int KK = decltype(kc)::value;
     if (W.split)
       k_cg_p_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph,
-                                                 W.pl, W.ks, first);
+                                                 W.pl, W.xh, W.xl, W.ks, first);
     else if (z_is_f32(P, W))
       k_cg_p<KK, float><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.p,
                                                      W.ks, first);
@@ -955,8 +989,8 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
 static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    k_cg_update_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.xh, W.xl, W.rh, W.rl, W.ph, W.pl, W.qh, W.ql,
-                                              L.dinv32, static_cast<float*>(W.u[0]), W.ks);
+    k_cg_update_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.rh, W.rl, W.qh, W.ql, L.dinv32,
+                                                    static_cast<float*>(W.u[0]), W.ks);
   });
   AMG_LAUNCH_CHECK();
 }
@@ -1176,7 +1210,14 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   stage_inputs(P, W, rq, st);
   if (o.cycle_precision == 64) pcg_loop<double>(owner, P, W, o, st);
   else pcg_loop<float>(owner, P, W, o, st);
-  if (W.split) launch_pair(false, (long long)W.n0 * K, nullptr, W.xh, W.xl, W.x, nullptr, st);
+  if (W.split) {
+    dispatch_k(K, [&](auto kc) {
+      constexpr int KK = decltype(kc)::value;
+      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.ph, W.pl, W.xh, W.xl, W.ks);
+    });
+    AMG_LAUNCH_CHECK();
+    launch_pair(false, (long long)W.n0 * K, nullptr, W.xh, W.xl, W.x, nullptr, st);
+  }
   stage_outputs(P, W, rq, W.x, st);
   // results
   int nv = P.nsys * K;
