@@ -118,6 +118,7 @@ struct TPart {
   int ncta = 0;
   int* cta_agg = nullptr;
   int rows_max = 0, p_max = 0, a_max = 0, c_max = 0;
+  int ra_max = 1;  // largest number of coarse dofs of one aggregate
   Stage sg;
 };
 

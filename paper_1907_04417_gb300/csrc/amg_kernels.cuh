@@ -297,6 +297,17 @@ __device__ __forceinline__ void df_acc(float ah, float al, float xh, float xl, f
   sh = s;
   sl += t + e;
 }
+// (sh, sl) += (ah, al) * x for an exact float x (unnormalised, as df_acc)
+__device__ __forceinline__ void df_acc1(float ah, float al, float x, float& sh, float& sl) {
+  float p = ah * x;
+  float e = fmaf(ah, x, -p);
+  e = fmaf(al, x, e);
+  float s = sh + p;
+  float v = s - sh;
+  float t = (sh - (s - v)) + (p - v);
+  sh = s;
+  sl += t + e;
+}
 __device__ __forceinline__ void df_norm(float& sh, float& sl) {
   float s, e;
   df_fast_two_sum(sh, sl, s, e);
@@ -425,15 +436,12 @@ __global__ void __launch_bounds__(BS) k_smooth(const int* __restrict__ cta_row, 
     int i = base + g;
     bool valid = i < r1;
     const size_t o = (size_t)i * K + cl * CPT;
-    TC fv[CPT], uv[CPT];
-    if (valid && nzl == 0) {
-      ldv<TC, CPT>(f + o, fv);
-      ldv<TC, CPT>(u + o, uv);
-    }
     TC acc[CPT];
     row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
     if (valid && nzl == 0) {
-      TC out[CPT];
+      TC fv[CPT], uv[CPT], out[CPT];
+      ldv<TC, CPT>(f + o, fv);
+      ldv<TC, CPT>(u + o, uv);
       TC di = __ldg(dinv + i);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[t], uv[t]);
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
                                                  const TC* __restrict__ u, TC* __restrict__ fc,
                                                  TC* __restrict__ uc, const TC* __restrict__ dinvc,
                                                  const int* __restrict__ done, int rows_max, int p_max,
-                                                 int a_max, Stage sg) {
+                                                 int a_max, Stage sg, int m_cs_max) {
   if (*done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char* tail = smraw + restrict_stage_bytes<TC>(sg);
@@ -510,11 +518,11 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
     int i = base + g;
     bool valid = i < r1;
     const size_t o = (size_t)i * K + cl * CPT;
-    TC fv[CPT];
-    if (valid && nzl == 0) ldv<TC, CPT>(f + o, fv);
     TC acc[CPT];
     row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
     if (valid && nzl == 0) {
+      TC fv[CPT];
+      ldv<TC, CPT>(f + o, fv);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) fv[t] -= acc[t];
       stv<TC, CPT>(tsm + (size_t)(i - r0) * K + cl * CPT, fv);
@@ -522,6 +530,37 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
   }
   __syncthreads();
   const int c0 = coarse_start[a0];
+  if constexpr (K >= 8) {
+    // one thread per (aggregate, 4 coarse dofs, column): four outputs in
+    // registers, one shared load of t per row, broadcast loads of P
+    const int nch = (m_cs_max + 3) / 4;
+    const int nwork = (a1 - a0) * nch * K;
+    for (int w = threadIdx.x; w < nwork; w += BS) {
+      const int c = w % K, q = (w / K) % nch, t = w / (K * nch);
+      const int ra = m_cs[t + 1] - m_cs[t], p0 = 4 * q;
+      if (p0 >= ra) continue;
+      const int rsl = m_rs[t], na = m_rs[t + 1] - rsl;
+      const TC* pa = psm + m_bk[t] + p0;
+      const TC* ta = tsm + (size_t)rsl * K + c;
+      TC acc[4] = {TC(0), TC(0), TC(0), TC(0)};
+      for (int i = 0; i < na; ++i) {
+        const TC tv = ta[(size_t)i * K];
+        const TC* prow = pa + i * ra;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+          if (p0 + p < ra) acc[p] = fma(prow[p], tv, acc[p]);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (p0 + p < ra) {
+          const int cd = c0 + m_cs[t] + p0 + p;
+          fc[(size_t)cd * K + c] = acc[p];
+          if (uc) uc[(size_t)cd * K + c] = acc[p] * __ldg(dinvc + cd);
+        }
+      }
+    }
+    return;
+  }
   const int nout = m_cs[a1 - a0] * K;
   for (int o = threadIdx.x; o < nout; o += BS) {
     int cdl = o / K, c = o % K;
@@ -741,7 +780,7 @@ __global__ void __launch_bounds__(BS) k_presmooth0(const int* __restrict__ cta_r
 // fused with r.z.  mode 0: rho = r.z (start); mode 1: beta = r.z / rho,
 // rho = r.z; mode 2: no scalars (a bare V-cycle).
 template <typename TC, int K, int NZL, bool DF>
-__global__ void __launch_bounds__(BS, 5) k_post0(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                               const int* __restrict__ col, const TC* __restrict__ val,
                                               const TC* __restrict__ dinv, const TC* __restrict__ f,
                                               const TC* __restrict__ u, const double* __restrict__ r,
@@ -769,8 +808,8 @@ __global__ void __launch_bounds__(BS, 5) k_post0(const int* __restrict__ cta_row
     int i = base + g;
     bool valid = i < r1;
     const size_t o = (size_t)i * K + cl * CPT;
-    // the row's own operands are loaded before its gathers so that their
-    // misses overlap
+    TC acc[CPT];
+    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
     TC fv[CPT], uv[CPT];
     float lv[NF];
     if (valid && nzl == 0) {
@@ -778,8 +817,6 @@ __global__ void __launch_bounds__(BS, 5) k_post0(const int* __restrict__ cta_row
       ldv<TC, CPT>(u + o, uv);
       if constexpr (DF) ldv<float, CPT>(rlo + o, lv);
     }
-    TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
     if constexpr (DF) {
       if (valid && nzl == 0) {
         TC zt[CPT];
@@ -787,7 +824,7 @@ __global__ void __launch_bounds__(BS, 5) k_post0(const int* __restrict__ cta_row
 #pragma unroll
         for (int t = 0; t < CPT; ++t) {
           zt[t] = fma(di, fv[t] - acc[t], uv[t]);
-          df_mac((float)fv[t], lv[t], (float)zt[t], 0.f, dh[t], dl[t]);
+          df_acc1((float)fv[t], lv[t], (float)zt[t], dh[t], dl[t]);
         }
         stv<TC, CPT>(z + o, zt);
       }
@@ -818,8 +855,12 @@ __global__ void __launch_bounds__(BS, 5) k_post0(const int* __restrict__ cta_row
   double dd[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
-    if constexpr (DF) dd[t] = (double)dh[t] + (double)dl[t];
-    else dd[t] = d[t];
+    if constexpr (DF) {
+      df_norm(dh[t], dl[t]);
+      dd[t] = (double)dh[t] + (double)dl[t];
+    } else {
+      dd[t] = d[t];
+    }
   }
   // lanes other than nzl == 0 hold zeros; reduce across the whole warp
   cta_colsum<K, CPT>(dd, sm, ks.partial + (size_t)blockIdx.x * K);

@@ -150,7 +150,7 @@ inline size_t csr_stage_bytes(const Stage& sg) {
                                           pvals<TC>(T), L.rowptr, L.col, vals<TC>(L), f, u, fc,        \
                                           smooth_next ? uc : nullptr,                                  \
                                           smooth_next ? dinvs<TC>(C) : nullptr, done, tp.rows_max,     \
-                                          tp.p_max, tp.a_max, tp.sg);                                  \
+                                          tp.p_max, tp.a_max, tp.sg, tp.ra_max);                       \
         } else {                                                                                       \
           throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
         }                                                                                              \

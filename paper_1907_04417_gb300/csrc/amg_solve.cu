@@ -3,6 +3,8 @@
 // replay of whole iterations, and the adjoint gradient kernel.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "amg_launch.cuh"
@@ -81,11 +83,6 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
     int i = base + g;
     bool valid = i < r1;
     const size_t o = (size_t)i * K + cl * CPT;
-    float hv[CPT], lv[CPT];
-    if (valid && nzl == 0) {
-      ldv<float, CPT>(ph + o, hv);
-      ldv<float, CPT>(pl + o, lv);
-    }
     float sh[CPT], sl[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) sh[t] = sl[t] = 0.f;
@@ -129,6 +126,9 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
         }
     }
     if (valid && nzl == 0) {
+      float hv[CPT], lv[CPT];
+      ldv<float, CPT>(ph + o, hv);
+      ldv<float, CPT>(pl + o, lv);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) df_mac(hv[t], lv[t], sh[t], sl[t], dh[t], dl[t]);
       stv<float, CPT>(qh + o, sh);
@@ -611,8 +611,8 @@ static RPart make_rpart(Arena& ar, const Level& L, long long target, const std::
   return p;
 }
 
-static TPart make_tpart(Arena& ar, const Transfer& T, const Level& F, int K, int* err) {
-  int target = K <= 2 ? 256 : (K <= 8 ? 128 : 64);
+static TPart make_tpart(Arena& ar, const Transfer& T, const Level& F, int K, int* err, int target = 0) {
+  if (target <= 0) target = K <= 2 ? 256 : (K <= 8 ? 128 : 64);
   std::vector<int> ca{0};
   int rows = 0;
   for (int a = 0; a < T.nagg; ++a) {
@@ -626,6 +626,7 @@ static TPart make_tpart(Arena& ar, const Transfer& T, const Level& F, int K, int
   ca.push_back(T.nagg);
   TPart tp;
   tp.ncta = (int)ca.size() - 1;
+  for (int a = 0; a < T.nagg; ++a) tp.ra_max = std::max(tp.ra_max, T.h_coarse_start[a + 1] - T.h_coarse_start[a]);
   for (int c = 0; c < tp.ncta; ++c) {
     int a0 = ca[c], a1 = ca[c + 1];
     tp.rows_max = std::max(tp.rows_max, T.h_row_start[a1] - T.h_row_start[a0]);
@@ -652,7 +653,17 @@ static int round_k(int nrhs) {
 // row-parallel kernels, chosen by timing the level's l1-Jacobi sweep with
 // every candidate on the workspace's own buffers (their contents do not
 // matter for timing).  The chosen layout serves every kernel of the level.
-static const long long kTargets[] = {512, 1024, 2048, 4096, 8192};
+static const long long kTargets[] = {256, 512, 1024, 2048, 4096, 8192};
+
+// AMG_TUNE_LOG=1 in the environment prints every candidate timing to stderr.
+static bool tune_log() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("AMG_TUNE_LOG");
+    on = (e && e[0] == '1') ? 1 : 0;
+  }
+  return on == 1;
+}
 
 template <typename TC>
 static std::vector<int> nzl_candidates(int K) {
@@ -672,13 +683,16 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
   AMG_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   long long bt = target_nnz(K);
-  int bn = W.nzl[k];
+  int bn = W.nzl[k], bs = 1;
   {
     Arena tmp;
     for (long long t : kTargets) {
-      RPart rp = make_rpart(tmp, L, t, sys, W.err);
-      if (t > kTargets[0] && rp.ncta < 152) break;  // fewer CTAs than SMs: stop growing
+      RPart rp0 = make_rpart(tmp, L, t, sys, W.err);
+      if (t > kTargets[0] && rp0.ncta < 152) break;  // fewer CTAs than SMs: stop growing
+      for (int stage = rp0.sg.enabled; stage >= 0; --stage)
       for (int n : nzl_candidates<TC>(K)) {
+        RPart rp = rp0;
+        rp.sg.enabled = stage;
         TC* f = static_cast<TC*>(W.f[k]);
         TC* u = static_cast<TC*>(W.u[k]);
         TC* v = static_cast<TC*>(W.v[k]);
@@ -689,10 +703,14 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
         AMG_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
         AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (tune_log())
+          fprintf(stderr, "[tune] level %d K %d smooth target %lld nzl %d stage %d ncta %d: %.1f us\n", k, K, t, n,
+                  stage, rp.ncta, ms * 1e3 / 3);
         if (ms < best) {
           best = ms;
           bt = t;
           bn = n;
+          bs = stage;
         }
       }
     }
@@ -700,8 +718,62 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (k == 0 && std::getenv("AMG_L0_TARGET")) bt = std::atoll(std::getenv("AMG_L0_TARGET"));
   W.rp[k] = make_rpart(W.ar, L, bt, sys, W.err);
+  W.rp[k].sg.enabled = W.rp[k].sg.enabled && bs;
   W.nzl[k] = bn;
+}
+
+// Per transfer: rows per CTA and staging of the fused residual + restriction.
+template <typename TC>
+static void tune_transfer(Plan& P, Workspace& W, int k) {
+  const int K = W.K;
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bt = 0, bs = 1;
+  {
+    Arena tmp;
+    for (int t : {32, 64, 128, 256, 512}) {
+      TPart tp0 = make_tpart(tmp, P.tr[k], P.lev[k], K, W.err, t);
+      if (t > 32 && tp0.ncta < 152) break;
+      for (int stage = tp0.sg.enabled; stage >= 0; --stage) {
+        TPart tp = tp0;
+        tp.sg.enabled = stage;
+        size_t smem = restrict_stage_bytes<TC>(tp.sg) +
+                      transfer_smem<TC>(tp.rows_max, tp.p_max, tp.a_max, tp.c_max, K, true);
+        if (smem > 200 * 1024) continue;
+        auto run = [&] {
+          launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], tp, P.lev[k + 1], k + 1 < P.L - 1,
+                              static_cast<TC*>(W.f[k]), static_cast<TC*>(W.u[k]), static_cast<TC*>(W.f[k + 1]),
+                              static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
+        };
+        run();
+        AMG_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 3; ++r) run();
+        AMG_CUDA(cudaEventRecord(e1, 0));
+        AMG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (tune_log())
+          fprintf(stderr, "[tune] level %d K %d restrict rows %d stage %d ncta %d: %.1f us\n", k, K, t, stage,
+                  tp.ncta, ms * 1e3 / 3);
+        if (ms < best) {
+          best = ms;
+          bt = t;
+          bs = stage;
+        }
+      }
+    }
+    AMG_CUDA(cudaDeviceSynchronize());
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bt > 0) {
+    W.tp[k] = make_tpart(W.ar, P.tr[k], P.lev[k], K, W.err, bt);
+    W.tp[k].sg.enabled = W.tp[k].sg.enabled && bs;
+  }
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
@@ -724,6 +796,7 @@ static void tune_q(Plan& P, Workspace& W) {
     AMG_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (tune_log()) fprintf(stderr, "[tune] q K %d nzl %d: %.1f us\n", W.K, n, ms * 1e3 / 3);
     if (ms < best) {
       best = ms;
       bn = n;
@@ -820,7 +893,13 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   AMG_CUDA(cudaMallocHost(&W->h_iter, sizeof(int)));
   for (int k = 0; k + 1 < P.L; ++k) W->tp.push_back(make_tpart(ar, P.tr[k], P.lev[k], K, W->err));
   AMG_CUDA(cudaDeviceSynchronize());
-  if (autotune) tune_q(P, *W);
+  if (autotune) {
+    for (int k = 0; k + 1 < P.L; ++k) {
+      if (prec == 64) tune_transfer<double>(P, *W, k);
+      else tune_transfer<float>(P, *W, k);
+    }
+    tune_q(P, *W);
+  }
   P.ws[key] = W;
   return *W;
 }
