@@ -24,6 +24,15 @@ Steps, each in the paper's order:
 * aggressive coarsening composes s consecutive pairwise steps into one
   aggregate map (Section 3, last paragraph; Section 5 composes several
   pairwise prolongators of the bootstrap hierarchy).
+
+The greedy matching is a 1/2-approximation of the paper's (auction-based)
+maximum product matching.  On the sparse, tree-like graphs of deep coarse
+levels it leaves many vertices unmatched, so a level whose composed steps
+shrink the node count by less than half of 2^s may be completed by
+``merge_singletons``: every aggregate made of a single node joins the
+aggregate of its most strongly coupled neighbour.  ``aggregate_operator``
+then forms the next level's graph with the w-weighted piecewise-constant
+prolongator (the pairwise P_c of Eq. (prol) extended to larger aggregates).
 """
 from __future__ import annotations
 
@@ -130,3 +139,42 @@ def aggregate_hierarchy(A: sp.csr_matrix, w: np.ndarray, steps_per_level, min_no
         aggs.append(comp.astype(np.int32))
         n_nodes.append(int(Ak.shape[0]))
     return aggs, n_nodes
+
+
+def merge_singletons(A: sp.csr_matrix, agg: np.ndarray) -> np.ndarray:
+    """Attach each single-node aggregate to the aggregate of its neighbour
+    with the largest |a_ij| (ties: lowest index); renumber by first member."""
+    agg = np.asarray(agg, dtype=np.int64).copy()
+    n = A.shape[0]
+    size = np.bincount(agg)
+    C = sp.coo_matrix(A)
+    off = C.row != C.col
+    r, c, v = C.row[off], C.col[off], np.abs(C.data[off])
+    single = size[agg] == 1
+    cand = single[r] & ~single[c]
+    r, c, v = r[cand], c[cand], v[cand]
+    if r.size:
+        order = np.lexsort((c, -v, r))
+        r, c = r[order], c[order]
+        first = np.unique(r, return_index=True)[1]
+        agg[r[first]] = agg[c[first]]
+    _, agg = np.unique(agg, return_inverse=True)
+    # renumber by smallest member so the map is canonical
+    first_member = np.full(agg.max() + 1, n, dtype=np.int64)
+    np.minimum.at(first_member, agg, np.arange(n))
+    rank = np.empty_like(first_member)
+    rank[np.argsort(first_member, kind="stable")] = np.arange(first_member.size)
+    return rank[agg]
+
+
+def aggregate_operator(A: sp.csr_matrix, w: np.ndarray, agg: np.ndarray):
+    """A_c = P^T A P and w_c = P^T w for the w-weighted piecewise-constant
+    prolongator of the aggregates ``agg``."""
+    n = A.shape[0]
+    nc = int(agg.max()) + 1
+    norm = np.sqrt(np.bincount(agg, weights=w * w, minlength=nc))
+    vals = np.where(norm[agg] > 0, w / np.where(norm[agg] > 0, norm[agg], 1.0), 1.0)
+    P = sp.csr_matrix((vals, (np.arange(n), agg)), shape=(n, nc))
+    Ac = (P.T @ A @ P).tocsr()
+    Ac.sort_indices()
+    return Ac, P.T @ w

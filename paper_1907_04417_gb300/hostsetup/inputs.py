@@ -63,16 +63,22 @@ def _rng(seed):
 
 def _levels_until(A, w, steps, m, max_coarse=1024, max_levels=12):
     """Compose ``steps`` pairwise steps per level, adding levels until
-    m * (number of aggregates) <= max_coarse."""
+    m * (number of aggregates) <= max_coarse.  A level whose steps shrink the
+    node count by less than half of 2^steps is completed by merging its
+    single-node aggregates into neighbouring ones."""
     aggs, n_nodes = [], [A.shape[0]]
     Ak, wk = A, np.asarray(w, dtype=np.float64)
     while len(aggs) < max_levels - 1:
+        A0, w0 = Ak, wk
         comp = np.arange(Ak.shape[0])
         for _ in range(steps):
             if Ak.shape[0] <= 1:
                 break
             agg, Ak, wk = aggregation.pairwise_step(Ak, wk)
             comp = agg[comp]
+        if A0.shape[0] > 2 and A0.shape[0] < 2 ** (steps - 1) * Ak.shape[0]:
+            comp = aggregation.merge_singletons(A0, comp)
+            Ak, wk = aggregation.aggregate_operator(A0, w0, comp)
         aggs.append(comp.astype(np.int32))
         n_nodes.append(int(Ak.shape[0]))
         if m * Ak.shape[0] <= max_coarse or Ak.shape[0] <= 2:

@@ -132,16 +132,24 @@ def elasticity(N: int, E: float = 1.0, nu: float = 0.3):
     N^3 node grid with 3 dofs per node, node-ordered (dof = 3*node + comp,
     as in the node-based ordering of Section 5.2).
 
-    Compact centred differences (times h^2):
+    Compact centred differences (times h^2), interior stencil:
       * same component c, direction d: graph-Laplacian edge of weight
         mu + (lambda + mu) * delta_cd between the two neighbouring nodes;
       * cross components c != d: u_d(p + s_c e_c + s_d e_d) enters row (p, c)
         with -(lambda + mu) s_c s_d / 4.
     The face x = 0 is clamped: the plane x = -1 is a Dirichlet plane whose
-    same-component edges stay on the diagonal.  On the other faces couplings
-    that leave the grid are dropped together with their diagonal part
-    (traction-free).  Returns A (SPD for N >= 2; checked numerically in the
-    tests)."""
+    same-component edges stay on the diagonal.  Elsewhere same-component
+    edges that leave the grid are dropped with their diagonal part.
+
+    Boundary closure of the cross terms (energy form): the entry between
+    (q, c) and (q', d) comes from the centred divergence at their common
+    neighbour o = q - s_c e_c = q' - s_d e_d, and is kept only where o is a
+    grid node whose centred differences in both directions c and d are
+    complete (each neighbour a grid node or on the clamped plane).  The
+    matrix is then mu * (clamped Laplacians) + (lambda + mu) * (sum over o of
+    (discrete div at o)^2 + per-line compact minus centred-wide second
+    differences), each part positive semi-definite, so A is SPD for every N.
+    Dropping out-of-grid couplings alone leaves A indefinite from N = 16."""
     lam = E * nu / ((1 + nu) * (1 - 2 * nu))
     mu = E / (2 * (1 + nu))
     I, J, K = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
@@ -171,7 +179,12 @@ def elasticity(N: int, E: float = 1.0, nu: float = 0.3):
             for sc in (1, -1):
                 for sd in (1, -1):
                     Q = P + sc * unit[c] + sd * unit[d]
-                    inside = np.all((Q >= 0) & (Q < N), axis=1)
+                    O = P + sc * unit[c]                     # centre of the divergence term
+                    inside = np.all((O >= 0) & (O < N), axis=1)
+                    for e in (c, d):
+                        lo = -1 if e == 0 else 0              # x = -1 is the clamped plane
+                        inside &= (O[:, e] - 1 >= lo) & (O[:, e] + 1 < N)
+                    inside &= np.all((Q >= 0) & (Q < N), axis=1)  # a clamped-plane value is 0
                     qn = (Q[inside, 0] * N + Q[inside, 1]) * N + Q[inside, 2]
                     rows.append(3 * node[inside] + c)
                     cols.append(3 * qn + d)

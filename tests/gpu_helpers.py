@@ -8,6 +8,19 @@ def oracle_coarse_start(Ho, k):
     return np.concatenate([[0], np.cumsum(Ho.levels[k].r)]).astype(np.int64)
 
 
+def _block_entries(e):
+    """Flatten the exported prolongator blocks of one level: for every stored
+    value its library fine row and library coarse column."""
+    r = e["r"].astype(np.int64)
+    rs = e["row_start"].astype(np.int64)
+    na = np.diff(rs)
+    size = na * r
+    t = np.repeat(np.arange(e["naggs"]), size)
+    loc = np.arange(size.sum()) - np.repeat(np.cumsum(size) - size, size)
+    col0 = np.cumsum(r) - r
+    return t, rs[t] + loc // r[t], col0[t] + loc % r[t]
+
+
 def level_maps(Hg, Ho):
     """For every level k: sigma_k (library dof -> oracle dof) and the signs
     s_k (library column = s_k * oracle column).  Also returns the exports."""
@@ -17,27 +30,17 @@ def level_maps(Hg, Ho):
     for k in range(1, Ho.L):
         e = ex[k]
         cs = oracle_coarse_start(Ho, k)
+        r = e["r"].astype(np.int64)
         r_orc = Ho.levels[k].r[e["agg_id"]]
-        assert np.array_equal(r_orc, e["r"]), "kept-column counts differ from the oracle"
-        s_map = np.concatenate([cs[a] + np.arange(r) for a, r in zip(e["agg_id"], e["r"])]).astype(np.int64)
+        assert np.array_equal(r_orc, r), "kept-column counts differ from the oracle"
+        owner = np.repeat(np.arange(e["naggs"]), r)
+        s_map = cs[e["agg_id"]][owner] + np.arange(r.sum()) - np.repeat(np.cumsum(r) - r, r)
+        _, frow, ccol = _block_entries(e)
         Porc = Ho.levels[k].P.tocsr()
-        signs = np.empty(e["n"])
-        off = 0
-        cpos = 0
-        rs = e["row_start"]
-        for t in range(e["naggs"]):
-            na = rs[t + 1] - rs[t]
-            r = e["r"][t]
-            blk = e["pval"][off:off + na * r].reshape(na, r)
-            rows_o = sig[k - 1][rs[t]:rs[t + 1]]
-            cols_o = s_map[cpos:cpos + r]
-            ob = Porc[rows_o][:, cols_o].toarray() * sgn[k - 1][rs[t]:rs[t + 1], None]
-            d = np.sum(blk * ob, axis=0)
-            signs[cpos:cpos + r] = np.where(d < 0, -1.0, 1.0)
-            off += na * r
-            cpos += r
-        sig.append(s_map)
-        sgn.append(signs)
+        ob = np.asarray(Porc[sig[k - 1][frow], s_map[ccol]]).ravel() * sgn[k - 1][frow]
+        d = np.bincount(ccol, weights=e["pval"] * ob, minlength=e["n"])
+        sig.append(s_map.astype(np.int64))
+        sgn.append(np.where(d < 0, -1.0, 1.0))
     return ex, sig, sgn
 
 
@@ -46,19 +49,13 @@ def compare_prolongators(Hg, Ho, atol=1e-10):
     worst = 0.0
     for k in range(1, Ho.L):
         e = ex[k]
-        rs = e["row_start"]
+        _, frow, ccol = _block_entries(e)
         Porc = Ho.levels[k].P.tocsr()
-        off = 0
-        cpos = 0
-        for t in range(e["naggs"]):
-            na = rs[t + 1] - rs[t]
-            r = e["r"][t]
-            blk = e["pval"][off:off + na * r].reshape(na, r)
-            ob = Porc[sig[k - 1][rs[t]:rs[t + 1]]][:, sig[k][cpos:cpos + r]].toarray()
-            ob = ob * sgn[k - 1][rs[t]:rs[t + 1], None] * sgn[k][None, cpos:cpos + r]
-            worst = max(worst, float(np.abs(blk - ob).max()))
-            off += na * r
-            cpos += r
+        ob = np.asarray(Porc[sig[k - 1][frow], sig[k][ccol]]).ravel()
+        # every nonzero of the oracle's P lies inside the library's block pattern
+        assert np.count_nonzero(ob) == np.count_nonzero(Porc.data)
+        ob = ob * sgn[k - 1][frow] * sgn[k][ccol]
+        worst = max(worst, float(np.abs(e["pval"] - ob).max(initial=0.0)))
     assert worst <= atol, worst
     return worst, ex, sig, sgn
 

@@ -85,3 +85,62 @@ def test_workload_builders_nested_maps():
 def test_elasticity_batch_same_depth():
     batch = inputs.elasticity_batch(n_sys=3, sides=(4, 5), nrhs=2, levels=3)
     assert len({P.levels for P in batch}) == 1
+
+
+def test_merge_singletons_joins_strongest_neighbour():
+    A = problems.cc5(12, problems.lognormal_field(12, 1.0, seed=9))
+    n = A.shape[0]
+    rng = np.random.default_rng(4)
+    agg = np.arange(n) // 2
+    single = rng.choice(n, 30, replace=False)
+    agg = agg.astype(np.int64)
+    agg[single] = n + np.arange(30)                 # thirty forced singletons
+    _, agg = np.unique(agg, return_inverse=True)
+    out = aggregation.merge_singletons(A, agg)
+    size_in = np.bincount(agg)
+    Ad = A.toarray()
+    for v in range(n):
+        if size_in[agg[v]] != 1:
+            continue
+        nb = [u for u in np.flatnonzero(Ad[v]) if u != v and size_in[agg[u]] > 1]
+        if not nb:
+            continue
+        best = min(nb, key=lambda u: (-abs(Ad[v, u]), u))
+        assert out[v] == out[best]
+    # aggregates of size > 1 stay together and apart
+    for a in np.flatnonzero(size_in > 1):
+        assert len(set(out[agg == a])) == 1
+    assert np.array_equal(np.unique(out), np.arange(out.max() + 1))
+    first = [np.flatnonzero(out == a)[0] for a in range(out.max() + 1)]
+    assert np.all(np.diff(first) > 0)
+
+
+def test_aggregate_operator_galerkin():
+    A = problems.poisson5(6)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, 36)
+    agg = np.arange(36) // 4
+    Ac, wc = aggregation.aggregate_operator(A, w, agg)
+    P = np.zeros((36, 9))
+    for a in range(9):
+        idx = np.flatnonzero(agg == a)
+        P[idx, a] = w[idx] / np.linalg.norm(w[idx])
+    np.testing.assert_allclose(Ac.toarray(), P.T @ A.toarray() @ P, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(P @ wc, w, rtol=1e-13)
+
+
+def test_cc_hierarchy_reaches_dense_limit():
+    P = inputs.diffusion_cc(128, nrhs=1)
+    assert 3 * P.n_nodes[-1] <= 1024 and len(P.n_nodes) <= 6
+
+
+@pytest.mark.parametrize("N", [16])
+def test_elasticity_spd_beyond_small_grids(N):
+    """Symmetric ordering, no pivoting: every pivot of the LU factorisation of
+    an SPD matrix is positive (a truncated cross stencil fails this at 16^3)."""
+    import scipy.sparse.linalg as spla
+    A = problems.elasticity(N)
+    assert abs(A - A.T).max() == 0
+    lu = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                   options=dict(SymmetricMode=True))
+    assert np.array_equal(lu.perm_r, lu.perm_c)
+    assert lu.U.diagonal().min() > 0
