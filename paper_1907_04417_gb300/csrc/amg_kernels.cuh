@@ -795,14 +795,17 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
   const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
   // DF: r = f + rlo exactly (double-float CG) and r.z is accumulated in
-  // double-float; otherwise r is float64
+  // double-float in per-thread shared-memory slots (registers stay free for
+  // the gathers); otherwise r is float64 and r.z a float64 register sum
   constexpr int ND = DF ? 1 : CPT, NF = DF ? CPT : 1;
+  __shared__ float sdot[2 * NF][BS];
   double d[ND];
-  float dh[NF], dl[NF];
 #pragma unroll
   for (int t = 0; t < ND; ++t) d[t] = 0;
+  if constexpr (DF) {
 #pragma unroll
-  for (int t = 0; t < NF; ++t) dh[t] = dl[t] = 0.f;
+    for (int t = 0; t < 2 * NF; ++t) sdot[t][threadIdx.x] = 0.f;
+  }
   const CsrView<TC> cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
@@ -822,11 +825,15 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
         TC zt[CPT];
         TC di = __ldg(dinv + i);
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-          zt[t] = fma(di, fv[t] - acc[t], uv[t]);
-          df_acc1((float)fv[t], lv[t], (float)zt[t], dh[t], dl[t]);
-        }
+        for (int t = 0; t < CPT; ++t) zt[t] = fma(di, fv[t] - acc[t], uv[t]);
         stv<TC, CPT>(z + o, zt);
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+          float h = sdot[t][threadIdx.x], l = sdot[NF + t][threadIdx.x];
+          df_acc1((float)fv[t], lv[t], (float)zt[t], h, l);
+          sdot[t][threadIdx.x] = h;
+          sdot[NF + t][threadIdx.x] = l;
+        }
       }
     } else if (valid && nzl == 0) {
       TC di = __ldg(dinv + i);
@@ -856,8 +863,7 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
     if constexpr (DF) {
-      df_norm(dh[t], dl[t]);
-      dd[t] = (double)dh[t] + (double)dl[t];
+      dd[t] = (double)sdot[t][threadIdx.x] + (double)sdot[NF + t][threadIdx.x];
     } else {
       dd[t] = d[t];
     }

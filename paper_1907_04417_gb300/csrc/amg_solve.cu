@@ -40,24 +40,29 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
 
 // q = A p in double-float on the float32 pipes: A as (val32, vallo), p as
 // (ph, pl), every product and sum error-free up to the final rounding of
-// the pair; q is stored in float64 and p.q is accumulated in double-float.
+// the pair; q is stored as a float pair and p.q is accumulated in
+// double-float.  The row loop is software-pipelined (the gathers of the next
+// non-zero are in flight while the current one is accumulated) and the p.q
+// accumulators live in shared memory, one slot per thread, so that four CTAs
+// fit on an SM.  Offsets into the n x K blocks are 32-bit (n K < 2^32 is
+// checked on the host).
 template <int K, int NZL>
-__global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
-                                                const int* __restrict__ col, const float* __restrict__ ahi,
-                                                const float* __restrict__ alo, const float* __restrict__ ph,
-                                                const float* __restrict__ pl, float* __restrict__ qh,
-                                                float* __restrict__ ql, KState ks) {
+__global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const float* __restrict__ ahi,
+                                                   const float* __restrict__ alo, const float* __restrict__ ph,
+                                                   const float* __restrict__ pl, float* __restrict__ qh,
+                                                   float* __restrict__ ql, KState ks, Stage sg) {
   if (*ks.done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
   __shared__ double tot[64];
   constexpr int CPT = VT<float, K>::CPT, CL = VT<float, K>::CL, G = NZL * CL, RPW = 32 / G;
+  __shared__ float sdot[2 * CPT][BS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
   const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
-  float dh[CPT], dl[CPT];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) dh[t] = dl[t] = 0.f;
+  for (int t = 0; t < 2 * CPT; ++t) sdot[t][threadIdx.x] = 0.f;
   // stage col, val_hi and val_lo of the CTA's rows
   const int* rp = rowptr;
   const int* cc = col;
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
     const void* dst[2];
     const int *srp, *scol;
     int j4, j8;
-    if (stage_csr<2>(ks.sg, smraw, r0, r1, rowptr, col, src, w, dst, srp, scol, j4, j8)) {
+    if (stage_csr<2>(sg, smraw, r0, r1, rowptr, col, src, w, dst, srp, scol, j4, j8)) {
       rp = srp;
       cc = scol;
       va = static_cast<const float*>(dst[0]);
@@ -79,39 +84,42 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
       joff = j4;
     }
   }
+  const unsigned lo = (unsigned)(cl * CPT);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
-    int i = base + g;
-    bool valid = i < r1;
-    const size_t o = (size_t)i * K + cl * CPT;
+    const int i = base + g;
+    const bool valid = i < r1;
     float sh[CPT], sl[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) sh[t] = sl[t] = 0.f;
     if (valid) {
-      int j1 = rp[i + 1 - roff] - joff;
+      const int j1 = rp[i + 1 - roff] - joff;
       int j = rp[i - roff] - joff + nzl;
-      for (; j + NZL < j1; j += 2 * NZL) {  // two non-zeros in flight
-        int c0 = cc[j], c1 = cc[j + NZL];
-        float ah0 = va[j], al0 = vb[j];
-        float ah1 = va[j + NZL], al1 = vb[j + NZL];
-        float xh0[CPT], xl0[CPT], xh1[CPT], xl1[CPT];
-        ldv<float, CPT>(ph + (size_t)c0 * K + cl * CPT, xh0);
-        ldv<float, CPT>(pl + (size_t)c0 * K + cl * CPT, xl0);
-        ldv<float, CPT>(ph + (size_t)c1 * K + cl * CPT, xh1);
-        ldv<float, CPT>(pl + (size_t)c1 * K + cl * CPT, xl1);
-#pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-          df_acc(ah0, al0, xh0[t], xl0[t], sh[t], sl[t]);
-          df_acc(ah1, al1, xh1[t], xl1[t], sh[t], sl[t]);
-        }
-      }
-      for (; j < j1; j += NZL) {
-        float ah = va[j], al = vb[j];
-        int c = cc[j];
+      if (j < j1) {
+        float a = va[j], b = vb[j];
         float xh[CPT], xl[CPT];
-        ldv<float, CPT>(ph + (size_t)c * K + cl * CPT, xh);
-        ldv<float, CPT>(pl + (size_t)c * K + cl * CPT, xl);
+        {
+          const unsigned off = (unsigned)cc[j] * (unsigned)K + lo;
+          ldv<float, CPT>(ph + off, xh);
+          ldv<float, CPT>(pl + off, xl);
+        }
+        for (j += NZL; j < j1; j += NZL) {
+          const float a2 = va[j], b2 = vb[j];
+          float yh[CPT], yl[CPT];
+          const unsigned off = (unsigned)cc[j] * (unsigned)K + lo;
+          ldv<float, CPT>(ph + off, yh);
+          ldv<float, CPT>(pl + off, yl);
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) df_acc(ah, al, xh[t], xl[t], sh[t], sl[t]);
+          for (int t = 0; t < CPT; ++t) df_acc(a, b, xh[t], xl[t], sh[t], sl[t]);
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) {
+            xh[t] = yh[t];
+            xl[t] = yl[t];
+          }
+          a = a2;
+          b = b2;
+        }
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) df_acc(a, b, xh[t], xl[t], sh[t], sl[t]);
       }
 #pragma unroll
       for (int t = 0; t < CPT; ++t) df_norm(sh[t], sl[t]);
@@ -126,18 +134,24 @@ __global__ void __launch_bounds__(BS) k_cg_q_df(const int* __restrict__ cta_row,
         }
     }
     if (valid && nzl == 0) {
+      const unsigned o = (unsigned)i * (unsigned)K + lo;
       float hv[CPT], lv[CPT];
       ldv<float, CPT>(ph + o, hv);
       ldv<float, CPT>(pl + o, lv);
-#pragma unroll
-      for (int t = 0; t < CPT; ++t) df_mac(hv[t], lv[t], sh[t], sl[t], dh[t], dl[t]);
       stv<float, CPT>(qh + o, sh);
       stv<float, CPT>(ql + o, sl);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        float h = sdot[t][threadIdx.x], l = sdot[CPT + t][threadIdx.x];
+        df_mac(hv[t], lv[t], sh[t], sl[t], h, l);
+        sdot[t][threadIdx.x] = h;
+        sdot[CPT + t][threadIdx.x] = l;
+      }
     }
   }
   double d[CPT];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) d[t] = (double)dh[t] + (double)dl[t];
+  for (int t = 0; t < CPT; ++t) d[t] = (double)sdot[t][threadIdx.x] + (double)sdot[CPT + t][threadIdx.x];
   cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
   if (!arrive_two_level(ks, RED_Q, K, sm, tot)) return;
   finish_alpha<K>(ks, sm, tot);
@@ -521,6 +535,9 @@ struct Workspace {
   int* h_done = nullptr;  // pinned
   std::vector<int> nzl;   // per level
   int nzl_q = 0;          // lanes per row of the level-0 q = A p
+  int q_stage = 1;        // whether the double-float q = A p stages its matrix slice
+  RPart rq{};             // level-0 row ranges of the double-float q = A p (own CTA size)
+  KState ksq{};           // the CG state seen through rq's CTA groups
   std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
   std::vector<RPart> rp;  // per level: row ranges for this column count
   int* err = nullptr;     // bounded-wait failures of the staged kernels
@@ -718,7 +735,6 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (k == 0 && std::getenv("AMG_L0_TARGET")) bt = std::atoll(std::getenv("AMG_L0_TARGET"));
   W.rp[k] = make_rpart(W.ar, L, bt, sys, W.err);
   W.rp[k].sg.enabled = W.rp[k].sg.enabled && bs;
   W.nzl[k] = bn;
@@ -780,15 +796,33 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
 
 // Lanes per row of the outer q = A p on the chosen level-0 layout (its CG
 // state is reset by the start of every solve, so timing runs are harmless).
+// The CG state seen through another level-0 partition: same scalars and
+// counters, the partition's CTA groups and its own partial sums.
+static KState view_state(Arena& ar, const KState& ks, const RPart& rp, int K) {
+  KState v = ks;
+  v.partial = ar.alloc<double>((size_t)rp.ncta * K);
+  v.gpartial = ar.alloc<double>((size_t)rp.ngroups * K);
+  v.gcount = ar.alloc<unsigned>((size_t)RED_KINDS * rp.ngroups);
+  AMG_CUDA(cudaMemset(v.gcount, 0, (size_t)RED_KINDS * rp.ngroups * sizeof(unsigned)));
+  v.grp_cta = rp.grp_cta;
+  v.sys_grp = rp.sys_grp;
+  v.ngroups = rp.ngroups;
+  v.sys_cta = rp.sys_cta;
+  v.sg = rp.sg;
+  return v;
+}
+
+// Level-0 q = A p: lanes per row, and for the double-float kernel also the
+// CTA size and staging, chosen by timing the kernel itself.
 static void tune_q(Plan& P, Workspace& W) {
   cudaEvent_t e0, e1;
   AMG_CUDA(cudaEventCreate(&e0));
   AMG_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bn = W.nzl_q;
+  int bn = W.nzl_q, bs = W.q_stage;
+  long long bt = -1;
   std::vector<int> cand = W.split ? nzl_candidates<float>(W.K) : nzl_candidates<double>(W.K);
-  for (int n : cand) {
-    W.nzl_q = n;
+  auto time_q = [&](const char* what, long long t, int n, int stage) {
     launch_cg_q(W, P.lev[0], 0);
     AMG_CUDA(cudaEventRecord(e0, 0));
     for (int r = 0; r < 3; ++r) launch_cg_q(W, P.lev[0], 0);
@@ -796,13 +830,55 @@ static void tune_q(Plan& P, Workspace& W) {
     AMG_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (tune_log()) fprintf(stderr, "[tune] q K %d nzl %d: %.1f us\n", W.K, n, ms * 1e3 / 3);
-    if (ms < best) {
-      best = ms;
-      bn = n;
+    if (tune_log())
+      fprintf(stderr, "[tune] q %s K %d target %lld nzl %d stage %d ncta %d: %.1f us\n", what, W.K, t, n, stage,
+              W.split ? W.rq.ncta : W.rp[0].ncta, ms * 1e3 / 3);
+    return ms;
+  };
+  if (!W.split) {
+    for (int n : cand) {
+      W.nzl_q = n;
+      float ms = time_q("f64", 0, n, 0);
+      if (ms < best) {
+        best = ms;
+        bn = n;
+      }
+    }
+    W.nzl_q = bn;
+  } else {
+    static const long long qTargets[] = {1024, 2048, 4096, 8192, 16384};
+    Arena tmp;
+    const RPart keep = W.rq;
+    const KState keep_ks = W.ksq;
+    for (long long t : qTargets) {
+      RPart rp = make_rpart(tmp, P.lev[0], t, P.h_sys_row, W.err);
+      if (t > qTargets[0] && rp.ncta < 4 * 152) break;  // under one wave of four CTAs per SM
+      W.rq = rp;
+      W.ksq = view_state(tmp, W.ks, rp, W.K);
+      for (int stage = rp.sg.enabled; stage >= 0; --stage)
+        for (int n : cand) {
+          W.nzl_q = n;
+          W.q_stage = stage;
+          float ms = time_q("df", t, n, stage);
+          if (ms < best) {
+            best = ms;
+            bn = n;
+            bs = stage;
+            bt = t;
+          }
+        }
+      AMG_CUDA(cudaDeviceSynchronize());
+    }
+    W.nzl_q = bn;
+    W.q_stage = bs;
+    if (bt > 0) {
+      W.rq = make_rpart(W.ar, P.lev[0], bt, P.h_sys_row, W.err);
+      W.ksq = view_state(W.ar, W.ks, W.rq, W.K);
+    } else {
+      W.rq = keep;
+      W.ksq = keep_ks;
     }
   }
-  W.nzl_q = bn;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
 }
@@ -821,6 +897,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   W->L = P.L;
   Arena& ar = W->ar;
   size_t n0k = (size_t)W->n0 * K;
+  AMG_REQUIRE(!split || n0k < (size_t(1) << 32), "n * nrhs must be below 2^32 for the float32-cycle solve");
   W->x = ar.alloc<double>(n0k);
   W->r = ar.alloc<double>(n0k);
   W->split = split;
@@ -892,6 +969,8 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   AMG_CUDA(cudaMallocHost(&W->h_done, sizeof(int)));
   AMG_CUDA(cudaMallocHost(&W->h_iter, sizeof(int)));
   for (int k = 0; k + 1 < P.L; ++k) W->tp.push_back(make_tpart(ar, P.tr[k], P.lev[k], K, W->err));
+  W->rq = W->rp[0];
+  W->ksq = view_state(ar, ks, W->rq, K);
   AMG_CUDA(cudaDeviceSynchronize());
   if (autotune) {
     for (int k = 0; k + 1 < P.L; ++k) {
@@ -1005,10 +1084,12 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
         constexpr int NZ = decltype(nc)::value;
         if constexpr (VT<float, KK>::CL * NZ <= 32) {
           auto kern = k_cg_q_df<KK, NZ>;
-          size_t smem = stage_bytes(W.rp[0].sg, 2, 0);
+          Stage sg = W.rq.sg;
+          sg.enabled = sg.enabled && W.q_stage;
+          size_t smem = stage_bytes(sg, 2, 0);
           ensure_smem(kern, smem);
-          kern<<<W.rp[0].ncta, BS, smem, st>>>(W.rp[0].cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.pl,
-                                               W.qh, W.ql, W.ks);
+          kern<<<W.rq.ncta, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.pl, W.qh,
+                                            W.ql, W.ksq, sg);
         }
       });
     });
@@ -1282,6 +1363,8 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, split, o.autotune != 0);
   W.ks.rtol = o.rtol;
   W.ks.maxit = o.maxit;
+  W.ksq.rtol = o.rtol;
+  W.ksq.maxit = o.maxit;
   StreamJoin sj(owner, user);
   cudaStream_t st = owner->own;
   std::vector<int> act(rq.nrhs.begin(), rq.nrhs.end());
