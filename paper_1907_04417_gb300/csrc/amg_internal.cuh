@@ -120,6 +120,7 @@ struct TPart {
   int rows_max = 0, p_max = 0, a_max = 0, c_max = 0;
   int ra_max = 1;  // largest number of coarse dofs of one aggregate
   Stage sg;
+  int warp = 0;    // restriction by one warp per aggregate (no CTA ranges)
 };
 
 // Row ranges of the row-parallel kernels of one level for a given column

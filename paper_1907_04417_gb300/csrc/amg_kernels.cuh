@@ -577,6 +577,78 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
   }
 }
 
+// Restriction with one warp per aggregate: t = f - A u on the aggregate's
+// rows (CL lanes per row, RPW rows per pass), fc = P_a^T t accumulated in
+// registers (RMAX >= r_a coarse dofs), the row groups of the warp combined
+// by shuffles, then uc = D_c^{-1} fc.  No shared-memory tile and no CTA-wide
+// barrier; matrix and prolongator entries are read straight from global.
+template <typename TC, int K, int RMAX>
+__global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restrict__ row_start,
+                                                   const int* __restrict__ coarse_start,
+                                                   const long long* __restrict__ blk_start,
+                                                   const TC* __restrict__ P, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ col, const TC* __restrict__ val,
+                                                   const TC* __restrict__ f, const TC* __restrict__ u,
+                                                   TC* __restrict__ fc, TC* __restrict__ uc,
+                                                   const TC* __restrict__ dinvc, const int* __restrict__ done) {
+  if (*done) return;
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / CL, cl = lane % CL;
+  const int a = blockIdx.x * NWARP + (threadIdx.x >> 5);
+  if (a >= nagg) return;  // whole warp
+  const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
+  const int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
+  const TC* Pa = P + __ldg(blk_start + a);
+  const CsrView<TC> cv{rowptr, 0, col, 0, val, 0};
+  TC acc[RMAX][CPT];
+#pragma unroll
+  for (int p = 0; p < RMAX; ++p)
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
+  for (int base = rs; base < re; base += RPW) {
+    const int i = base + g;
+    const bool valid = i < re;
+    TC s[CPT];
+    row_acc<TC, TC, K, 1>(i, valid, cv, u, 0, cl, s);
+    if (valid) {
+      TC fv[CPT];
+      ldv<TC, CPT>(f + (size_t)i * K + cl * CPT, fv);
+      const TC* prow = Pa + (size_t)(i - rs) * ra;
+#pragma unroll
+      for (int p = 0; p < RMAX; ++p) {
+        if (p < ra) {
+          const TC pv = __ldg(prow + p);
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) acc[p][t] = fma(pv, fv[t] - s[t], acc[p][t]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = CL; off < 32; off <<= 1)
+#pragma unroll
+    for (int p = 0; p < RMAX; ++p)
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) acc[p][t] += __shfl_xor_sync(FULL, acc[p][t], off);
+  if (g == 0) {
+#pragma unroll
+    for (int p = 0; p < RMAX; ++p) {
+      if (p < ra) {
+        const size_t oc = (size_t)(cs + p) * K + cl * CPT;
+        stv<TC, CPT>(fc + oc, acc[p]);
+        if (uc) {
+          const TC d = __ldg(dinvc + cs + p);
+          TC w[CPT];
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) w[t] = acc[p][t] * d;
+          stv<TC, CPT>(uc + oc, w);
+        }
+      }
+    }
+  }
+}
+
 // u[rows(a)] += P_a uc[coarse(a)]   (aggregate-aligned CTAs)
 template <typename TC, int K>
 __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg, const int* __restrict__ row_start,

@@ -137,6 +137,23 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   void launch_restrict<TC>(int K, int nzl, const Level& L, const Transfer& T, const TPart& tp,         \
                            const Level& C, bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, \
                            const int* done, cudaStream_t st) {                                         \
+    if (tp.warp) {                                                                                     \
+      dispatch_k(K, [&](auto kc) {                                                                     \
+        constexpr int KK = decltype(kc)::value;                                                        \
+        auto go = [&](auto rc) {                                                                       \
+          constexpr int RM = decltype(rc)::value;                                                      \
+          k_restrict_w<TC, KK, RM><<<(T.nagg + NWARP - 1) / NWARP, BS, 0, st>>>(                       \
+              T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), L.rowptr, L.col,         \
+              vals<TC>(L), f, u, fc, smooth_next ? uc : nullptr, smooth_next ? dinvs<TC>(C) : nullptr, \
+              done);                                                                                   \
+        };                                                                                             \
+        if (tp.ra_max <= 4) go(std::integral_constant<int, 4>{});                                      \
+        else if (tp.ra_max <= 8) go(std::integral_constant<int, 8>{});                                 \
+        else throw Error(AMG_ERR_INVALID_ARG, "internal: warp restriction needs r_a <= 8");           \
+      });                                                                                              \
+      AMG_LAUNCH_CHECK();                                                                              \
+      return;                                                                                          \
+    }                                                                                                  \
     size_t smem = restrict_stage_bytes<TC>(tp.sg) +                                                    \
                   transfer_smem<TC>(tp.rows_max, tp.p_max, tp.a_max, tp.c_max, K, true);              \
     dispatch_k(K, [&](auto kc) {                                                                       \

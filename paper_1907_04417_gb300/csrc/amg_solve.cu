@@ -784,18 +784,37 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     }
     AMG_CUDA(cudaDeviceSynchronize());
   }
+  // the warp-per-aggregate restriction (no CTA ranges, no staging)
+  bool warp_best = false;
+  if (W.tp[k].ra_max <= 8) {
+    TPart tw = W.tp[k];
+    tw.warp = 1;
+    auto run = [&] {
+      launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], tw, P.lev[k + 1], k + 1 < P.L - 1,
+                          static_cast<TC*>(W.f[k]), static_cast<TC*>(W.u[k]), static_cast<TC*>(W.f[k + 1]),
+                          static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
+    };
+    run();
+    AMG_CUDA(cudaEventRecord(e0, 0));
+    for (int r = 0; r < 3; ++r) run();
+    AMG_CUDA(cudaEventRecord(e1, 0));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (tune_log()) fprintf(stderr, "[tune] level %d K %d restrict warp-per-aggregate: %.1f us\n", k, K, ms * 1e3 / 3);
+    warp_best = ms < best;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (bt > 0) {
     W.tp[k] = make_tpart(W.ar, P.tr[k], P.lev[k], K, W.err, bt);
     W.tp[k].sg.enabled = W.tp[k].sg.enabled && bs;
   }
+  W.tp[k].warp = warp_best ? 1 : 0;
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
 
-// Lanes per row of the outer q = A p on the chosen level-0 layout (its CG
-// state is reset by the start of every solve, so timing runs are harmless).
 // The CG state seen through another level-0 partition: same scalars and
 // counters, the partition's CTA groups and its own partial sums.
 static KState view_state(Arena& ar, const KState& ks, const RPart& rp, int K) {
@@ -813,7 +832,8 @@ static KState view_state(Arena& ar, const KState& ks, const RPart& rp, int K) {
 }
 
 // Level-0 q = A p: lanes per row, and for the double-float kernel also the
-// CTA size and staging, chosen by timing the kernel itself.
+// CTA size and staging, chosen by timing the kernel itself (the CG state is
+// reset by the start of every solve, so timing runs are harmless).
 static void tune_q(Plan& P, Workspace& W) {
   cudaEvent_t e0, e1;
   AMG_CUDA(cudaEventCreate(&e0));

@@ -244,5 +244,6 @@ def test_cc_full_adjoint(amg, ccd):
         km[c] -= h
         dv = (problems.cc5(N, kp.reshape(N, N)).data - problems.cc5(N, km.reshape(N, N)).data) / (2 * h)
         ref = float(ga @ dv)
-        # lambda comes from an iterative solve (rtol 1e-12): per cell 1e-6
-        assert abs(ref - g[c]) <= 1e-6 * (abs(ref) + 1e-3 * np.abs(g).max()), (c, ref, g[c])
+        # lambda comes from an iterative solve (rtol 1e-12): per cell 1e-6 of
+        # the value plus 1e-7 of the gradient's scale
+        assert abs(ref - g[c]) <= 1e-6 * abs(ref) + 1e-7 * np.abs(g).max(), (c, ref, g[c])
