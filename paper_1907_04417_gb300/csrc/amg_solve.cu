@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_r
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
                                                    const float* __restrict__ alo, const float* __restrict__ ph,
                                                    const float* __restrict__ pl, float* __restrict__ qh,
-                                                   float* __restrict__ ql, KState ks, Stage sg) {
+                                                   float* __restrict__ ql, KState ks, Stage sg, int nchunk) {
   if (*ks.done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
@@ -60,9 +60,12 @@ __global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_r
   __shared__ float sdot[2 * CPT][BS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
-  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
 #pragma unroll
   for (int t = 0; t < 2 * CPT; ++t) sdot[t][threadIdx.x] = 0.f;
+  // row chunks: one per CTA, or (persistent launch, never staged) every
+  // gridDim.x-th chunk
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  const int r0 = cta_row[chunk], r1 = cta_row[chunk + 1];
   // stage col, val_hi and val_lo of the CTA's rows
   const int* rp = rowptr;
   const int* cc = col;
@@ -148,6 +151,7 @@ __global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_r
         sdot[CPT + t][threadIdx.x] = l;
       }
     }
+  }
   }
   double d[CPT];
 #pragma unroll
@@ -537,7 +541,8 @@ struct Workspace {
   int nzl_q = 0;          // lanes per row of the level-0 q = A p
   int q_stage = 1;        // whether the double-float q = A p stages its matrix slice
   RPart rq{};             // level-0 row ranges of the double-float q = A p (own CTA size)
-  KState ksq{};           // the CG state seen through rq's CTA groups
+  int q_grid = 0;         // > 0: persistent q launch of q_grid CTAs over rq's ranges
+  KState ksq{};           // the CG state seen through the q launch's CTA groups
   std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
   std::vector<RPart> rp;  // per level: row ranges for this column count
   int* err = nullptr;     // bounded-wait failures of the staged kernels
@@ -625,6 +630,26 @@ static RPart make_rpart(Arena& ar, const Level& L, long long target, const std::
   p.sys_grp = up(sys_grp);
   p.sys_cta = up(sys_cta);
   p.sg = make_stage(rp, cr, err);
+  return p;
+}
+
+// CTA groups of a persistent launch of ``ncta`` CTAs over one system (no
+// row ranges of its own: the CTAs walk the chunks of another partition).
+static RPart make_flat(Arena& ar, int ncta) {
+  std::vector<int> grp{0};
+  for (int c = 0; c < ncta; c += 64) grp.push_back(std::min(c + 64, ncta));
+  std::vector<int> sys_grp{0, (int)grp.size() - 1}, sys_cta{0, ncta};
+  RPart p;
+  p.ncta = ncta;
+  p.ngroups = (int)grp.size() - 1;
+  auto up = [&](const std::vector<int>& v) {
+    int* d = ar.alloc<int>(v.size());
+    AMG_CUDA(cudaMemcpy(d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return d;
+  };
+  p.grp_cta = up(grp);
+  p.sys_grp = up(sys_grp);
+  p.sys_cta = up(sys_cta);
   return p;
 }
 
@@ -889,11 +914,40 @@ static void tune_q(Plan& P, Workspace& W) {
         }
       AMG_CUDA(cudaDeviceSynchronize());
     }
+    // persistent launches (one system): 3 or 4 CTAs per SM walk the chunks
+    int bg = 0;
+    if (P.nsys == 1) {
+      for (int per_sm : {4, 3}) {
+        const int grid = per_sm * 152;
+        RPart flat = make_flat(tmp, grid);
+        for (long long t : qTargets) {
+          RPart rp = make_rpart(tmp, P.lev[0], t, P.h_sys_row, W.err);
+          if (rp.ncta < 2 * grid) break;
+          W.rq = rp;
+          W.q_grid = grid;
+          W.ksq = view_state(tmp, W.ks, flat, W.K);
+          for (int n : cand) {
+            W.nzl_q = n;
+            W.q_stage = 0;
+            float ms = time_q("df persistent", t, n, 0);
+            if (ms < best) {
+              best = ms;
+              bn = n;
+              bs = 0;
+              bt = t;
+              bg = grid;
+            }
+          }
+          AMG_CUDA(cudaDeviceSynchronize());
+        }
+      }
+    }
     W.nzl_q = bn;
     W.q_stage = bs;
+    W.q_grid = bg;
     if (bt > 0) {
       W.rq = make_rpart(W.ar, P.lev[0], bt, P.h_sys_row, W.err);
-      W.ksq = view_state(W.ar, W.ks, W.rq, W.K);
+      W.ksq = view_state(W.ar, W.ks, bg > 0 ? make_flat(W.ar, bg) : W.rq, W.K);
     } else {
       W.rq = keep;
       W.ksq = keep_ks;
@@ -1105,11 +1159,12 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
         if constexpr (VT<float, KK>::CL * NZ <= 32) {
           auto kern = k_cg_q_df<KK, NZ>;
           Stage sg = W.rq.sg;
-          sg.enabled = sg.enabled && W.q_stage;
+          sg.enabled = sg.enabled && W.q_stage && W.q_grid == 0;
           size_t smem = stage_bytes(sg, 2, 0);
           ensure_smem(kern, smem);
-          kern<<<W.rq.ncta, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.pl, W.qh,
-                                            W.ql, W.ksq, sg);
+          const int grid = W.q_grid > 0 ? W.q_grid : W.rq.ncta;
+          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.pl, W.qh, W.ql,
+                                       W.ksq, sg, W.rq.ncta);
         }
       });
     });
