@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
                                               const TC* __restrict__ dinv, const TC* __restrict__ f,
                                               const TC* __restrict__ u, const double* __restrict__ r,
                                               const float* __restrict__ rlo, TC* __restrict__ z, KState ks,
-                                              int mode, Stage sg) {
+                                              int mode, Stage sg, int nchunk) {
   if (*ks.done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
@@ -865,7 +865,6 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, G = NZL * CL, RPW = 32 / G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
-  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
   // DF: r = f + rlo exactly (double-float CG) and r.z is accumulated in
   // double-float in per-thread shared-memory slots (registers stay free for
   // the gathers); otherwise r is float64 and r.z a float64 register sum
@@ -878,6 +877,10 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
 #pragma unroll
     for (int t = 0; t < 2 * NF; ++t) sdot[t][threadIdx.x] = 0.f;
   }
+  // one row range per CTA, or (persistent launch, one system, never staged)
+  // every gridDim.x-th range
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  const int r0 = cta_row[chunk], r1 = cta_row[chunk + 1];
   const CsrView<TC> cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
@@ -929,6 +932,7 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
       }
       stv<TC, CPT>(z + o, zt);
     }
+  }
   }
   if (mode == 2) return;
   double dd[CPT];

@@ -98,7 +98,7 @@ template <typename TC>
 void launch_coarse(int K, const Coarsest& C, const TC* f, TC* u, const int* done, cudaStream_t st);
 template <typename TC>
 void launch_post0(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u, const double* r,
-                  const float* rlo, TC* z, const KState& ks, int mode, cudaStream_t st);
+                  const float* rlo, TC* z, const KState& ks, int mode, cudaStream_t st, int grid = 0);
 template <typename TC>
 void launch_update(int K, const Level& L, const RPart& rp, double* x, double* r, const double* p,
                    const double* q, TC* u0, TC* f0, const KState& ks, cudaStream_t st);
@@ -202,7 +202,7 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   template <>                                                                                          \
   void launch_post0<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,    \
                         const double* r, const float* rlo, TC* z, const KState& ks, int mode,          \
-                        cudaStream_t st) {                                                             \
+                        cudaStream_t st, int grid) {                                                   \
     size_t smem = csr_stage_bytes<TC>(rp.sg);                                                          \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
@@ -211,8 +211,9 @@ inline size_t csr_stage_bytes(const Stage& sg) {
         if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
           auto kern = rlo ? k_post0<TC, KK, NZ, true> : k_post0<TC, KK, NZ, false>;                    \
           ensure_smem(kern, smem);                                                                     \
-          kern<<<rp.ncta, BS, smem, st>>>(rp.cta_row, L.rowptr, L.col, vals<TC>(L), dinvs<TC>(L), f,   \
-                                          u, r, rlo, z, ks, mode, rp.sg);                              \
+          kern<<<grid > 0 ? grid : rp.ncta, BS, smem, st>>>(rp.cta_row, L.rowptr, L.col, vals<TC>(L), \
+                                                            dinvs<TC>(L), f, u, r, rlo, z, ks, mode,   \
+                                                            rp.sg, rp.ncta);                           \
         } else {                                                                                       \
           throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
         }                                                                                              \

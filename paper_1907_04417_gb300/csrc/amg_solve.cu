@@ -312,13 +312,11 @@ template <int K>
 __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta_row, float* __restrict__ rh,
                                                      float* __restrict__ rl, const float* __restrict__ qh,
                                                      const float* __restrict__ ql, const float* __restrict__ dinv,
-                                                     float* __restrict__ u0, KState ks) {
+                                                     float* __restrict__ u0, KState ks, int nchunk) {
   if (*ks.done) return;
   __shared__ double sm[BS];
   __shared__ double tot[64];
   constexpr int CPT = VT<float, K>::CPT;
-  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
-  const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
   const int cfirst = (int)((threadIdx.x * CPT) % K);
   const int s = cta_system(ks.sys_cta, ks.nsys);
   float ah[CPT], al[CPT], dh[CPT], dl[CPT];
@@ -327,6 +325,10 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
     split2(-ks.alpha[s * K + cfirst + t], ah[t], al[t]);
     dh[t] = dl[t] = 0.f;
   }
+  // one row range per CTA, or (persistent launch, one system) every
+  // gridDim.x-th range
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
     float ra[CPT], rb[CPT], qa[CPT], qb[CPT], uo[CPT];
     ldp<float, CPT>(rh + e, ra);
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
     stv<float, CPT>(rl + e, rb);
     stv<float, CPT>(u0 + e, uo);
   }
+  }
   double d[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) d[t] = (double)dh[t] + (double)dl[t];
@@ -360,11 +363,9 @@ template <int K>
 __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
                                                 float* __restrict__ ph, float* __restrict__ pl,
                                                 float* __restrict__ xh, float* __restrict__ xl, KState ks,
-                                                int first) {
+                                                int first, int nchunk) {
   if (*ks.done) return;
   constexpr int CPT = VT<float, K>::CPT;
-  const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
-  const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
   const int cfirst = (int)((threadIdx.x * CPT) % K);
   const int s = cta_system(ks.sys_cta, ks.nsys);
   float bh[CPT], bl[CPT], ah[CPT], al[CPT];
@@ -373,6 +374,8 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
     split2(ks.beta[s * K + cfirst + t], bh[t], bl[t]);
     split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
   }
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
     float zv[CPT], pa[CPT], pb[CPT];
     ldv<float, CPT>(z + e, zv);
@@ -401,6 +404,7 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
     }
     stv<float, CPT>(ph + e, pa);
     stv<float, CPT>(pl + e, pb);
+  }
   }
 }
 
@@ -542,6 +546,9 @@ struct Workspace {
   int q_stage = 1;        // whether the double-float q = A p stages its matrix slice
   RPart rq{};             // level-0 row ranges of the double-float q = A p (own CTA size)
   int q_grid = 0;         // > 0: persistent q launch of q_grid CTAs over rq's ranges
+  int pers_grid = 0;      // CTAs of the persistent level-0 launches below (one system)
+  int upd_pers = 0, p_pers = 0, post_pers = 0;  // which level-0 kernels run persistent
+  KState ksf{};           // the CG state seen through the persistent launches' CTA groups
   KState ksq{};           // the CG state seen through the q launch's CTA groups
   std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
   std::vector<RPart> rp;  // per level: row ranges for this column count
@@ -957,6 +964,63 @@ static void tune_q(Plan& P, Workspace& W) {
   cudaEventDestroy(e1);
 }
 
+static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st);
+static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, cudaStream_t st);
+
+// Level-0 kernels of the double-float CG (one system): each runs either one
+// CTA per row range or persistent (four CTAs per SM walking the ranges, one
+// reduction per CTA), whichever the timing favours.  The timing runs use a
+// private all-stopped flag, cleared before every launch, so that the stopping
+// test of a reducing kernel cannot turn the following launches into no-ops.
+static void tune_persist(Plan& P, Workspace& W) {
+  const int K = W.K;
+  W.pers_grid = 4 * 152;
+  W.ksf = view_state(W.ar, W.ks, make_flat(W.ar, W.pers_grid), K);
+  int* tdone = W.ar.alloc<int>(1);
+  int* keep_done = W.ks.done;
+  W.ks.done = tdone;
+  W.ksf.done = tdone;
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  auto timeit = [&](const char* what, int pers, auto launch) {
+    AMG_CUDA(cudaMemsetAsync(tdone, 0, sizeof(int), 0));
+    launch();
+    AMG_CUDA(cudaEventRecord(e0, 0));
+    for (int r = 0; r < 3; ++r) {
+      AMG_CUDA(cudaMemsetAsync(tdone, 0, sizeof(int), 0));
+      launch();
+    }
+    AMG_CUDA(cudaEventRecord(e1, 0));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (tune_log()) fprintf(stderr, "[tune] %s K %d persistent %d: %.1f us\n", what, K, pers, ms * 1e3 / 3);
+    return ms;
+  };
+  auto pick = [&](const char* what, int& flag, auto launch) {
+    flag = 0;
+    float a = timeit(what, 0, launch);
+    flag = 1;
+    float b = timeit(what, 1, launch);
+    flag = b < a ? 1 : 0;
+  };
+  pick("update", W.upd_pers, [&] { launch_update_df(W, P.lev[0], 0); });
+  pick("p", W.p_pers, [&] { launch_cg_p(P, W, P.lev[0], 0, 0); });
+  pick("post", W.post_pers, [&] {
+    RPart rp0 = W.rp[0];
+    if (W.post_pers) rp0.sg.enabled = 0;
+    launch_post0<float>(K, W.nzl[0], P.lev[0], rp0, static_cast<float*>(W.f[0]), static_cast<float*>(W.u[0]),
+                        W.r, W.rl, reinterpret_cast<float*>(W.z), W.post_pers ? W.ksf : W.ks, 1, 0,
+                        W.post_pers ? W.pers_grid : 0);
+  });
+  AMG_CUDA(cudaDeviceSynchronize());
+  W.ks.done = keep_done;
+  W.ksf.done = keep_done;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false) {
   long long key = ((long long)split << 40) | ((long long)K << 32) | ((long long)prec << 16) |
                   ((long long)pre << 8) | post;
@@ -1052,6 +1116,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
       else tune_transfer<float>(P, *W, k);
     }
     tune_q(P, *W);
+    if (split && P.nsys == 1) tune_persist(P, *W);
   }
   P.ws[key] = W;
   return *W;
@@ -1146,8 +1211,11 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     res = cur[k];
   }
   TimedLaunch tl(h, AMG_KERNEL_SMOOTH_L0, st, pool);
-  launch_post0<TC>(K, W.nzl[0], P.lev[0], W.rp[0], F(0), cur[0], W.r, W.split ? W.rl : nullptr,
-                   reinterpret_cast<TC*>(W.z), ks, mode, st);
+  const bool pers = W.post_pers && &ks == &W.ks;
+  RPart rp0 = W.rp[0];
+  if (pers) rp0.sg.enabled = 0;
+  launch_post0<TC>(K, W.nzl[0], P.lev[0], rp0, F(0), cur[0], W.r, W.split ? W.rl : nullptr,
+                   reinterpret_cast<TC*>(W.z), pers ? W.ksf : ks, mode, st, pers ? W.pers_grid : 0);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
@@ -1210,8 +1278,8 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     if (W.split)
-      k_cg_p_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph,
-                                                 W.pl, W.xh, W.xl, W.ks, first);
+      k_cg_p_df<KK><<<W.p_pers ? W.pers_grid : W.rp[0].ncta, BS, 0, st>>>(
+          W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph, W.pl, W.xh, W.xl, W.ks, first, W.rp[0].ncta);
     else if (z_is_f32(P, W))
       k_cg_p<KK, float><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.p,
                                                      W.ks, first);
@@ -1224,8 +1292,9 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
 static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    k_cg_update_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.rh, W.rl, W.qh, W.ql, L.dinv32,
-                                                    static_cast<float*>(W.u[0]), W.ks);
+    k_cg_update_df<KK><<<W.upd_pers ? W.pers_grid : W.rp[0].ncta, BS, 0, st>>>(
+        W.rp[0].cta_row, W.rh, W.rl, W.qh, W.ql, L.dinv32, static_cast<float*>(W.u[0]),
+        W.upd_pers ? W.ksf : W.ks, W.rp[0].ncta);
   });
   AMG_LAUNCH_CHECK();
 }
@@ -1436,10 +1505,10 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   const int K = round_k(maxr);
   const bool split = o.cycle_precision == 32 && !o.outer_fp64 && P.L > 1;
   Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, split, o.autotune != 0);
-  W.ks.rtol = o.rtol;
-  W.ks.maxit = o.maxit;
-  W.ksq.rtol = o.rtol;
-  W.ksq.maxit = o.maxit;
+  for (KState* v : {&W.ks, &W.ksq, &W.ksf}) {  // the state and its views over other CTA groups
+    v->rtol = o.rtol;
+    v->maxit = o.maxit;
+  }
   StreamJoin sj(owner, user);
   cudaStream_t st = owner->own;
   std::vector<int> act(rq.nrhs.begin(), rq.nrhs.end());
