@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--maxit", type=int, default=5000)
     ap.add_argument("--roofline-kernel", default="auto")
+    ap.add_argument("--tune-cache", default=None,
+                    help="file of tuned launch choices: read when it has this workload, else written "
+                         "(so that a profiled run replays the choices of a plain run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--profile-kernels", action="store_true",
@@ -281,6 +284,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
+    if args.tune_cache:
+        os.environ["AMG_TUNE_CACHE"] = args.tune_cache
     import numpy as np
     import torch
 

@@ -549,6 +549,13 @@ struct Workspace {
   int pers_grid = 0;      // CTAs of the persistent level-0 launches below (one system)
   int upd_pers = 0, p_pers = 0, post_pers = 0;  // which level-0 kernels run persistent
   KState ksf{};           // the CG state seen through the persistent launches' CTA groups
+  // the tuned choices, as applied (written to and read from the tuning cache)
+  std::vector<long long> t_rp;  // per smoothed level: target, stage, lanes
+  std::vector<int> t_rps, t_nzl;
+  std::vector<int> t_tp, t_tps, t_tpw;  // per transfer: rows target (0: default), stage, warp kernel
+  long long t_q = 0;                    // q: target (0: level-0 ranges), lanes, stage, persistent grid
+  int t_qn = 0, t_qs = 0, t_qg = 0;
+  int t_pg = 0, t_pu = 0, t_pp = 0, t_ppost = 0;  // persistent grid and flags of update / p / post
   KState ksq{};           // the CG state seen through the q launch's CTA groups
   std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
   std::vector<RPart> rp;  // per level: row ranges for this column count
@@ -723,6 +730,102 @@ static std::vector<int> nzl_candidates(int K) {
   return v;
 }
 
+// ------------------------------------------------- tuned choices, applied --
+// Each tuner ends by applying its choice through these, and a choice read
+// back from the tuning cache takes the same path.
+static void apply_level(Plan& P, Workspace& W, int k, long long target, int stage, int nzl) {
+  std::vector<int> sys = (k == 0) ? P.h_sys_row : std::vector<int>{0, P.lev[k].n};
+  W.rp[k] = make_rpart(W.ar, P.lev[k], target, sys, W.err);
+  W.rp[k].sg.enabled = W.rp[k].sg.enabled && stage;
+  W.nzl[k] = nzl;
+  W.t_rp[k] = target;
+  W.t_rps[k] = stage;
+  W.t_nzl[k] = nzl;
+}
+static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, int warp) {
+  if (target > 0) {
+    W.tp[k] = make_tpart(W.ar, P.tr[k], P.lev[k], W.K, W.err, target);
+    W.tp[k].sg.enabled = W.tp[k].sg.enabled && stage;
+  }
+  W.tp[k].warp = warp;
+  W.t_tp[k] = target;
+  W.t_tps[k] = stage;
+  W.t_tpw[k] = warp;
+}
+static KState view_state(Arena& ar, const KState& ks, const RPart& rp, int K);
+static RPart make_flat(Arena& ar, int ncta);
+static void apply_q(Plan& P, Workspace& W, long long target, int nzl, int stage, int grid) {
+  W.nzl_q = nzl;
+  W.q_stage = stage;
+  W.q_grid = grid;
+  if (target > 0) {
+    W.rq = make_rpart(W.ar, P.lev[0], target, P.h_sys_row, W.err);
+    W.ksq = view_state(W.ar, W.ks, grid > 0 ? make_flat(W.ar, grid) : W.rq, W.K);
+  }
+  W.t_q = target;
+  W.t_qn = nzl;
+  W.t_qs = stage;
+  W.t_qg = grid;
+}
+static void apply_persist(Workspace& W, int grid, int upd, int p, int post) {
+  if (grid > 0) {
+    W.pers_grid = grid;
+    W.ksf = view_state(W.ar, W.ks, make_flat(W.ar, grid), W.K);
+  }
+  W.upd_pers = upd;
+  W.p_pers = p;
+  W.post_pers = post;
+  W.t_pg = grid;
+  W.t_pu = upd;
+  W.t_pp = p;
+  W.t_ppost = post;
+}
+
+// Tuning cache: when the environment variable AMG_TUNE_CACHE names a file,
+// a workspace whose problem shape (level sizes, systems, columns, precision,
+// sweeps) has a line there takes its choices from that line instead of
+// timing them, and newly tuned choices are appended to it.
+static std::string tune_key(const Plan& P, int K, int prec, int pre, int post, bool split) {
+  std::string k = "amg-tune-1 K" + std::to_string(K) + " prec" + std::to_string(prec) + " split" +
+                  std::to_string(split ? 1 : 0) + " sweeps" + std::to_string(pre) + "/" + std::to_string(post) +
+                  " nsys" + std::to_string(P.nsys) + " levels";
+  for (int l = 0; l < P.L; ++l) k += " " + std::to_string(P.lev[l].n) + ":" + std::to_string(P.lev[l].nnz);
+  return k;
+}
+static bool tune_cache_load(const std::string& key, std::vector<long long>& vals) {
+  const char* path = std::getenv("AMG_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return false;
+  char line[8192];
+  bool found = false;
+  while (std::fgets(line, sizeof line, fp)) {
+    std::string sl(line);
+    size_t bar = sl.find(" | ");
+    if (bar == std::string::npos || sl.compare(0, bar, key) != 0 || bar != key.size()) continue;
+    vals.clear();
+    const char* c = sl.c_str() + bar + 3;
+    char* end = nullptr;
+    for (long long v = std::strtoll(c, &end, 10); end != c; v = std::strtoll(c, &end, 10)) {
+      vals.push_back(v);
+      c = end;
+    }
+    found = true;  // the last matching line wins
+  }
+  std::fclose(fp);
+  return found;
+}
+static void tune_cache_store(const std::string& key, const std::vector<long long>& vals) {
+  const char* path = std::getenv("AMG_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = std::fopen(path, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s |", key.c_str());
+  for (long long v : vals) std::fprintf(fp, " %lld", v);
+  std::fprintf(fp, "\n");
+  std::fclose(fp);
+}
+
 template <typename TC>
 static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys) {
   const Level& L = P.lev[k];
@@ -767,9 +870,7 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  W.rp[k] = make_rpart(W.ar, L, bt, sys, W.err);
-  W.rp[k].sg.enabled = W.rp[k].sg.enabled && bs;
-  W.nzl[k] = bn;
+  apply_level(P, W, k, bt, bs, bn);
 }
 
 // Per transfer: rows per CTA and staging of the fused residual + restriction.
@@ -838,11 +939,7 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (bt > 0) {
-    W.tp[k] = make_tpart(W.ar, P.tr[k], P.lev[k], K, W.err, bt);
-    W.tp[k].sg.enabled = W.tp[k].sg.enabled && bs;
-  }
-  W.tp[k].warp = warp_best ? 1 : 0;
+  apply_transfer(P, W, k, bt, bs, warp_best ? 1 : 0);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
@@ -896,7 +993,7 @@ static void tune_q(Plan& P, Workspace& W) {
         bn = n;
       }
     }
-    W.nzl_q = bn;
+    apply_q(P, W, 0, bn, 0, 0);
   } else {
     static const long long qTargets[] = {1024, 2048, 4096, 8192, 16384};
     Arena tmp;
@@ -949,16 +1046,9 @@ static void tune_q(Plan& P, Workspace& W) {
         }
       }
     }
-    W.nzl_q = bn;
-    W.q_stage = bs;
-    W.q_grid = bg;
-    if (bt > 0) {
-      W.rq = make_rpart(W.ar, P.lev[0], bt, P.h_sys_row, W.err);
-      W.ksq = view_state(W.ar, W.ks, bg > 0 ? make_flat(W.ar, bg) : W.rq, W.K);
-    } else {
-      W.rq = keep;
-      W.ksq = keep_ks;
-    }
+    W.rq = keep;
+    W.ksq = keep_ks;
+    apply_q(P, W, bt, bn, bs, bg);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -974,8 +1064,7 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
 // test of a reducing kernel cannot turn the following launches into no-ops.
 static void tune_persist(Plan& P, Workspace& W) {
   const int K = W.K;
-  W.pers_grid = 4 * 152;
-  W.ksf = view_state(W.ar, W.ks, make_flat(W.ar, W.pers_grid), K);
+  apply_persist(W, 4 * 152, 0, 0, 0);
   int* tdone = W.ar.alloc<int>(1);
   int* keep_done = W.ks.done;
   W.ks.done = tdone;
@@ -1019,6 +1108,8 @@ static void tune_persist(Plan& P, Workspace& W) {
   W.ksf.done = keep_done;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  apply_persist(W, 0, W.upd_pers, W.p_pers, W.post_pers);
+  W.t_pg = W.pers_grid;
 }
 
 static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false) {
@@ -1070,7 +1161,20 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     W->nzl[k] = prec == 64 ? pick_nzl<double>(P.lev[k], K) : pick_nzl<float>(P.lev[k], K);
   }
   W->nzl_q = split ? pick_nzl<float>(P.lev[0], K) : pick_nzl<double>(P.lev[0], K);
-  if (autotune) {
+  const int nt = std::max(P.L - 1, 0);
+  W->t_rp.assign(P.L, 0);
+  W->t_rps.assign(P.L, 0);
+  W->t_nzl.assign(P.L, 0);
+  W->t_tp.assign(nt, 0);
+  W->t_tps.assign(nt, 0);
+  W->t_tpw.assign(nt, 0);
+  // cached choices: per smoothed level 3, per transfer 3, q 4, persistent 4
+  const std::string tkey = tune_key(P, K, prec, pre, post, split);
+  std::vector<long long> tv;
+  const bool cached = autotune && tune_cache_load(tkey, tv) && tv.size() == (size_t)(6 * nt + 8);
+  if (cached) {
+    for (int k = 0; k < nt; ++k) apply_level(P, *W, k, tv[3 * k], (int)tv[3 * k + 1], (int)tv[3 * k + 2]);
+  } else if (autotune) {
     for (int k = 0; k + 1 < P.L; ++k) {  // smoothed levels (the coarsest has no smoother)
       std::vector<int> sys = (k == 0) ? P.h_sys_row : std::vector<int>{0, P.lev[k].n};
       if (prec == 64) tune_level<double>(P, *W, k, sys);
@@ -1110,13 +1214,26 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   W->rq = W->rp[0];
   W->ksq = view_state(ar, ks, W->rq, K);
   AMG_CUDA(cudaDeviceSynchronize());
-  if (autotune) {
+  if (cached) {
+    const long long* t = tv.data() + 3 * nt;
+    for (int k = 0; k < nt; ++k) apply_transfer(P, *W, k, (int)t[3 * k], (int)t[3 * k + 1], (int)t[3 * k + 2]);
+    t += 3 * nt;
+    if (t[0] > 0 || t[1] > 0) apply_q(P, *W, t[0], (int)t[1], (int)t[2], (int)t[3]);
+    t += 4;
+    if (split && P.nsys == 1) apply_persist(*W, (int)t[0], (int)t[1], (int)t[2], (int)t[3]);
+  } else if (autotune) {
     for (int k = 0; k + 1 < P.L; ++k) {
       if (prec == 64) tune_transfer<double>(P, *W, k);
       else tune_transfer<float>(P, *W, k);
     }
     tune_q(P, *W);
     if (split && P.nsys == 1) tune_persist(P, *W);
+    std::vector<long long> out;
+    for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_rp[k], W->t_rps[k], W->t_nzl[k]});
+    for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_tp[k], W->t_tps[k], W->t_tpw[k]});
+    out.insert(out.end(), {W->t_q, W->t_qn, W->t_qs, W->t_qg});
+    out.insert(out.end(), {W->t_pg, W->t_pu, W->t_pp, W->t_ppost});
+    tune_cache_store(tkey, out);
   }
   P.ws[key] = W;
   return *W;
