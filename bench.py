@@ -200,8 +200,8 @@ def algorithmic_bytes(kernel, lv, K, wc):
     roofline section of the design notes): matrix arrays once, each vector
     block once per read or write, prolongator blocks once."""
     n0, nnz0, n1, npv = lv["n0"], lv["nnz0"], lv["n1"], lv["npv1"]
-    if kernel == "spmv_cg":      # q = A p (float64), p.q
-        return nnz0 * 12 + 4 * (n0 + 1) + 2 * n0 * K * 8
+    if kernel == "spmv_cg":      # q = A p (A as a float pair, p float32, q a float pair), p.q
+        return nnz0 * 12 + 4 * (n0 + 1) + n0 * K * 4 + n0 * K * 8
     if kernel == "restrict_l0":  # t = f - A u, fc = P^T t, uc = D^-1 fc
         return nnz0 * (wc + 4) + 4 * (n0 + 1) + 2 * n0 * K * wc + npv * wc + n1 * (2 * K * wc + wc)
     if kernel == "smooth_l0":    # z = u + D^-1 (f - A u), r.z

@@ -86,6 +86,11 @@ struct Level {
   int max_row_len = 0;
   double avg_row_len = 0;
   std::vector<int> h_rowptr;  // host copy of rowptr (partitions)
+  // row groups (coarse levels): the coarse dofs of one aggregate share one
+  // column pattern and are stored back to back; gstart (ngrp + 1 rows) is
+  // the coarse_start of the transfer that made the level
+  int grp_ok = 0, ngrp = 0, grp_rmax = 0;
+  const int* gstart = nullptr;
 };
 
 // P^{k+1}: maps level k+1 (coarse) to level k (fine).
@@ -99,6 +104,7 @@ struct Transfer {
   float* p32 = nullptr;
   std::vector<int> h_row_start, h_coarse_start;
   std::vector<long long> h_blk_start;
+  int* gagg = nullptr;  // nagg + 1: first row group of the fine level in each aggregate (grouped fine levels)
 };
 
 // Capacities of the shared-memory staging of a CTA's CSR slice (see
@@ -120,7 +126,9 @@ struct TPart {
   int rows_max = 0, p_max = 0, a_max = 0, c_max = 0;
   int ra_max = 1;  // largest number of coarse dofs of one aggregate
   Stage sg;
-  int warp = 0;    // restriction by one warp per aggregate (no CTA ranges)
+  int warp = 0;    // restriction: 0 CTA ranges, 1 one warp per aggregate, 2 grouped (one CTA per aggregate)
+  int pwarp = 0;   // prolongation by one warp per aggregate (no CTA ranges)
+  int jl = 1;      // grouped restriction: lanes splitting a group's pattern columns
 };
 
 // Row ranges of the row-parallel kernels of one level for a given column
@@ -156,6 +164,7 @@ struct Plan {
   int* perm0 = nullptr;        // library row -> row within its own system (caller numbering)
   std::unique_ptr<Arena> arena;
   std::map<long long, std::shared_ptr<Workspace>> ws;
+  bool groups_done = false;    // row groups of the coarse levels detected
   Plan() : arena(new Arena) {}
   ~Plan();
 };

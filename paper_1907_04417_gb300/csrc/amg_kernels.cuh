@@ -117,6 +117,66 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase)
   return ok != 0;
 }
 
+// Double-buffered staging for CTAs that walk several row chunks (persistent
+// launches): while the CTA works on chunk c from buffer c & 1, the rowptr,
+// col and value slices (4-byte values) of its next chunk arrive in the other
+// buffer by 1-D bulk TMA copies, each buffer completing on its own mbarrier.
+// Layout: two mbarriers (16 bytes), then per buffer rows_max + 8 rowptr
+// words and span4 words of col and of each of the NV value arrays.  Copies
+// start at 16-byte boundaries (rowptr words from r0 & ~3, non-zeros from
+// j0 & ~3) and stay inside the arrays' padding.
+__host__ __device__ inline size_t pipe_buf_bytes(const Stage& sg, int nv) {
+  return align16((size_t)(sg.rows_max + 8) * 4) + (size_t)sg.span4 * 4 * (1 + nv);
+}
+__host__ __device__ inline size_t pipe_bytes(const Stage& sg, int nv, int nbuf) {
+  return sg.enabled ? 16 + (size_t)nbuf * pipe_buf_bytes(sg, nv) : 0;
+}
+__device__ __forceinline__ void pipe_init(unsigned char* smem) {
+  if (threadIdx.x == 0) {
+    mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
+    mbar_init(reinterpret_cast<uint64_t*>(smem) + 1, 1);
+  }
+  __syncthreads();
+}
+// One thread: request rows [r0, r1) into buffer buf.
+template <int NV>
+__device__ __forceinline__ void pipe_issue(const Stage& sg, unsigned char* smem, int buf, int r0, int r1,
+                                           const int* __restrict__ rowptr, const int* __restrict__ col,
+                                           const float* const (&vals)[NV]) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + buf;
+  unsigned char* b = smem + 16 + (size_t)buf * pipe_buf_bytes(sg, NV);
+  const int a0 = r0 & ~3, a1 = (r1 + 4) & ~3;
+  const int j0 = __ldg(rowptr + r0), j1 = __ldg(rowptr + r1);
+  const int e0 = j0 & ~3, e1 = (j1 + 3) & ~3;
+  const unsigned rb = (unsigned)(a1 - a0) * 4u, cb = (unsigned)(e1 - e0) * 4u;
+  // the buffer's previous contents were read through the generic proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, rb + cb * (1u + NV));
+  tma_load_1d(b, rowptr + a0, rb, bar);
+  unsigned char* c = b + align16((size_t)(sg.rows_max + 8) * 4);
+  tma_load_1d(c, col + e0, cb, bar);
+#pragma unroll
+  for (int a = 0; a < NV; ++a) tma_load_1d(c + (size_t)sg.span4 * 4 * (1 + a), vals[a] + e0, cb, bar);
+}
+// All threads: wait for buffer buf (its use-th fill) and return its views.
+template <int NV>
+__device__ __forceinline__ void pipe_wait(const Stage& sg, unsigned char* smem, int buf, int use, int r0,
+                                          const int* __restrict__ rowptr, const int*& rp, int& roff,
+                                          const int*& cs, const float* (&vs)[NV], int& joff) {
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + buf;
+  if (!mbar_wait_bounded(bar, (unsigned)(use & 1))) {
+    atomicOr(sg.err, 1);
+    mbar_wait_bounded(bar, (unsigned)(use & 1));
+  }
+  unsigned char* b = smem + 16 + (size_t)buf * pipe_buf_bytes(sg, NV);
+  rp = reinterpret_cast<const int*>(b);
+  roff = r0 & ~3;
+  cs = reinterpret_cast<const int*>(b + align16((size_t)(sg.rows_max + 8) * 4));
+#pragma unroll
+  for (int a = 0; a < NV; ++a) vs[a] = reinterpret_cast<const float*>(cs + (size_t)sg.span4 * (1 + a));
+  joff = __ldg(rowptr + r0) & ~3;
+}
+
 // Where the row loop reads rowptr / col / values: either the staged copies
 // (with index offsets) or the global arrays.
 template <typename TA>
@@ -177,16 +237,53 @@ __device__ __forceinline__ bool stage_csr(const Stage& sg, unsigned char* smem, 
   return true;
 }
 
+// Gathers a lane keeps in flight per row pass: with one lane group per row
+// (NZL = 1) the whole of a short row (a 9-point stencil row, or a 10-entry
+// slice of a longer one) is requested before the first product, so a row
+// costs one memory round trip; with the non-zeros split over NZL lanes each
+// lane has few of them and four at a time suffice.
+template <int NZL>
+__host__ __device__ constexpr int gather_depth() { return NZL == 1 ? 10 : 4; }
+
 // y_i = sum_j a_ij x_j for the K columns owned by this lane.
 template <typename TA, typename TX, int K, int NZL>
 __device__ __forceinline__ void row_acc(int i, bool valid, const CsrView<TA>& cv, const TX* __restrict__ x,
                                         int nzl, int cl, TX (&acc)[VT<TX, K>::CPT]) {
-  constexpr int CPT = VT<TX, K>::CPT, CL = VT<TX, K>::CL;
+  constexpr int CPT = VT<TX, K>::CPT, CL = VT<TX, K>::CL, U = gather_depth<NZL>();
 #pragma unroll
   for (int t = 0; t < CPT; ++t) acc[t] = TX(0);
   if (valid) {
     const int j1 = cv.rp[i + 1 - cv.roff];
     int j = cv.rp[i - cv.roff] + nzl;
+    if constexpr (U != 4) {
+      // predicated batches of U non-zeros: every gather of the batch is
+      // issued before the first product
+      for (; j < j1; j += U * NZL) {
+        int c[U];
+        TX a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int jj = j + u * NZL;
+          const bool ok = jj < j1;
+          c[u] = ok ? cv.col[jj - cv.coff] : -1;
+          a[u] = ok ? (TX)cv.val[jj - cv.voff] : TX(0);
+        }
+        TX xv[U][CPT];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (c[u] >= 0) {
+            ldv<TX, CPT>(x + (size_t)c[u] * K + cl * CPT, xv[u]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) xv[u][t] = TX(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) acc[t] = fma(a[u], xv[u][t], acc[t]);
+      }
+    } else {
     // four non-zeros at a time: their gathers are independent and issue
     // back to back
     for (; j + 3 * NZL < j1; j += 4 * NZL) {
@@ -212,6 +309,7 @@ __device__ __forceinline__ void row_acc(int i, bool valid, const CsrView<TA>& cv
       ldv<TX, CPT>(x + (size_t)c * K + cl * CPT, xv);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) acc[t] = fma(a, xv[t], acc[t]);
+    }
     }
   }
   if constexpr (NZL > 1) {
@@ -324,6 +422,54 @@ __device__ __forceinline__ void df_add(float& sh, float& sl, float oh, float ol)
 __device__ __forceinline__ void df_split(double v, float& h, float& l) {
   h = (float)v;
   l = (float)(v - (double)h);
+}
+
+// Packed float32 pairs: two columns per instruction with the add / sub /
+// mul / fma .f32x2 forms of sm_100 and later, each half rounded to nearest
+// exactly as its scalar form, so a packed double-float step gives the same
+// bits as two scalar ones.
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ F2 f2_pack(float a, float b) {
+  F2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(F2 x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  F2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b) {
+  F2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  F2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
+  F2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ F2 f2_neg(F2 a) { return F2{a.v ^ 0x8000000080000000ull}; }
+// df_acc1 on a pair of columns (the same steps as the scalar form)
+__device__ __forceinline__ void df_acc1_x2(F2 ah, F2 al, F2 x, F2& sh, F2& sl) {
+  const F2 p = f2_mul(ah, x);
+  F2 e = f2_fma(ah, x, f2_neg(p));
+  e = f2_fma(al, x, e);
+  const F2 s = f2_add(sh, p);
+  const F2 v = f2_sub(s, sh);
+  const F2 t = f2_add(f2_sub(sh, f2_sub(s, v)), f2_sub(p, v));
+  sh = s;
+  sl = f2_add(sl, f2_add(t, e));
 }
 
 // CG scalars shared by the fused kernels.
@@ -649,6 +795,179 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
   }
 }
 
+// ----------------------------------------------- grouped coarse levels --
+// On a Galerkin level every coarse dof of one aggregate (a row group) has
+// the same column pattern: the coarse dofs of all neighbouring aggregates,
+// in one order, S columns per row, the rows of the group stored back to back
+// (row p of the group at rowptr[g0] + p S).  The kernels below gather each
+// of the S rows of u once per group and apply it to all RA (at most) rows of
+// the group, instead of once per row.  A slot of CL * JL lanes owns one
+// group: CL lanes split the K columns (CPT each), JL lanes split the S
+// pattern columns (lane jl takes j = jl, jl + JL, ...) and are combined by
+// shuffles; there are 32 / (CL JL) slots per warp.
+constexpr int GATHER_G = 10;  // gathers in flight per lane in the grouped kernels
+
+template <typename TC, int K, int RA, int JL>
+__device__ __forceinline__ void group_acc(int r0, int ra, const int* __restrict__ rowptr,
+                                          const int* __restrict__ col, const TC* __restrict__ val,
+                                          const TC* __restrict__ x, int cl, int jl,
+                                          TC (&acc)[RA][VT<TC, K>::CPT]) {
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, U = GATHER_G;
+#pragma unroll
+  for (int p = 0; p < RA; ++p)
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
+  const int base = __ldg(rowptr + r0), S = __ldg(rowptr + r0 + 1) - base;
+  for (int j = jl; j < S; j += U * JL) {
+    TC xv[U][CPT];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = j + u * JL;
+      if (jj < S) {
+        ldv<TC, CPT>(x + (size_t)__ldg(col + base + jj) * K + cl * CPT, xv[u]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) xv[u][t] = TC(0);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < RA; ++p) {
+      if (p < ra) {
+        const TC* vp = val + base + (size_t)p * S;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int jj = j + u * JL;
+          const TC a = jj < S ? __ldg(vp + jj) : TC(0);
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) acc[p][t] = fma(a, xv[u][t], acc[p][t]);
+        }
+      }
+    }
+  }
+  if constexpr (JL > 1) {
+#pragma unroll
+    for (int off = CL; off < CL * JL; off <<= 1)
+#pragma unroll
+      for (int p = 0; p < RA; ++p)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) acc[p][t] += __shfl_xor_sync(FULL, acc[p][t], off);
+  }
+}
+
+// v = u + D^{-1} (f - A u) on a grouped level (one l1-Jacobi sweep).
+template <typename TC, int K, int RA, int JL>
+__global__ void __launch_bounds__(BS) k_smooth_g(int ngrp, const int* __restrict__ gstart,
+                                                 const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                 const TC* __restrict__ val, const TC* __restrict__ dinv,
+                                                 const TC* __restrict__ f, const TC* __restrict__ u,
+                                                 TC* __restrict__ v, const int* __restrict__ done) {
+  if (*done) return;
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, SPW = 32 / (CL * JL);
+  const int lane = threadIdx.x & 31, cl = lane % CL, jl = (lane / CL) % JL;
+  const int g = (blockIdx.x * NWARP + (threadIdx.x >> 5)) * SPW + lane / (CL * JL);
+  // a slot past the last group computes nothing but stays for the shuffles
+  const bool live = g < ngrp;
+  const int r0 = live ? __ldg(gstart + g) : 0, ra = live ? __ldg(gstart + g + 1) - r0 : 0;
+  TC acc[RA][CPT];
+  if (live || JL > 1) group_acc<TC, K, RA, JL>(r0, live ? ra : 0, rowptr, col, val, u, cl, live ? jl : 1 << 30, acc);
+  if (!live || jl != 0) return;
+#pragma unroll
+  for (int p = 0; p < RA; ++p) {
+    if (p < ra) {
+      const int i = r0 + p;
+      const size_t o = (size_t)i * K + cl * CPT;
+      TC fv[CPT], uv[CPT], out[CPT];
+      ldv<TC, CPT>(f + o, fv);
+      ldv<TC, CPT>(u + o, uv);
+      const TC di = __ldg(dinv + i);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[p][t], uv[t]);
+      stv<TC, CPT>(v + o, out);
+    }
+  }
+}
+
+// Fused residual + restriction out of a grouped level, one CTA of
+// RG_WARPS warps per coarse aggregate: each slot takes row groups of the
+// aggregate in turn, forms t = f - A u on the group's rows and accumulates
+// fc += P_a^T t over them (RMAX >= r_a coarse dofs); the slots are combined
+// by shuffles and then across warps in shared memory, in a fixed order, and
+// uc = D_c^{-1} fc is written when the coarse level is smoothed.
+constexpr int RG_WARPS = 4;
+template <typename TC, int K, int RA, int RMAX, int JL>
+__global__ void __launch_bounds__(RG_WARPS * 32) k_restrict_g(
+    int nagg, const int* __restrict__ row_start, const int* __restrict__ coarse_start,
+    const long long* __restrict__ blk_start, const TC* __restrict__ P, const int* __restrict__ gstart,
+    const int* __restrict__ gagg, const int* __restrict__ rowptr, const int* __restrict__ col,
+    const TC* __restrict__ val, const TC* __restrict__ f, const TC* __restrict__ u, TC* __restrict__ fc,
+    TC* __restrict__ uc, const TC* __restrict__ dinvc, const int* __restrict__ done) {
+  if (*done) return;
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, SPW = 32 / (CL * JL), NSLOT = RG_WARPS * SPW;
+  __shared__ TC red[RG_WARPS][RMAX][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, cl = lane % CL, jl = (lane / CL) % JL;
+  const int slot = warp * SPW + lane / (CL * JL);
+  const int a = blockIdx.x;
+  const int rs = __ldg(row_start + a), cs = __ldg(coarse_start + a), rc = __ldg(coarse_start + a + 1) - cs;
+  const TC* Pa = P + __ldg(blk_start + a);
+  TC accp[RMAX][CPT];
+#pragma unroll
+  for (int q = 0; q < RMAX; ++q)
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) accp[q][t] = TC(0);
+  const int g0 = __ldg(gagg + a), g1 = __ldg(gagg + a + 1);
+  // every slot runs the same number of passes (the shuffles inside group_acc
+  // need the whole warp); a slot without a group in a pass adds nothing
+  const int passes = (g1 - g0 + NSLOT - 1) / NSLOT;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int g = g0 + ps * NSLOT + slot;
+    const bool live = g < g1;
+    const int r0 = live ? __ldg(gstart + g) : 0, ra = live ? __ldg(gstart + g + 1) - r0 : 0;
+    TC acc[RA][CPT];
+    group_acc<TC, K, RA, JL>(r0, ra, rowptr, col, val, u, cl, live ? jl : 1 << 30, acc);
+    if (jl == 0) {
+#pragma unroll
+      for (int p = 0; p < RA; ++p) {
+        if (p < ra) {
+          const int i = r0 + p;
+          TC fv[CPT];
+          ldv<TC, CPT>(f + (size_t)i * K + cl * CPT, fv);
+          const TC* prow = Pa + (size_t)(i - rs) * rc;
+#pragma unroll
+          for (int q = 0; q < RMAX; ++q) {
+            if (q < rc) {
+              const TC pv = __ldg(prow + q);
+#pragma unroll
+              for (int t = 0; t < CPT; ++t) accp[q][t] = fma(pv, fv[t] - acc[p][t], accp[q][t]);
+            }
+          }
+        }
+      }
+    }
+  }
+  // lanes with jl != 0 hold zeros; combine the slots of the warp
+#pragma unroll
+  for (int off = CL; off < 32; off <<= 1)
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q)
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) accp[q][t] += __shfl_xor_sync(FULL, accp[q][t], off);
+  if (lane < CL)
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q)
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) red[warp][q][cl * CPT + t] = accp[q][t];
+  __syncthreads();
+  for (int e = threadIdx.x; e < rc * K; e += RG_WARPS * 32) {
+    const int q = e / K, c = e % K;
+    TC s = red[0][q][c];
+#pragma unroll
+    for (int w = 1; w < RG_WARPS; ++w) s += red[w][q][c];
+    const size_t oc = (size_t)(cs + q) * K + c;
+    fc[oc] = s;
+    if (uc) uc[oc] = s * __ldg(dinvc + cs + q);
+  }
+}
+
 // u[rows(a)] += P_a uc[coarse(a)]   (aggregate-aligned CTAs)
 template <typename TC, int K>
 __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg, const int* __restrict__ row_start,
@@ -694,6 +1013,45 @@ __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg,
     ldp<TC, CPT>(up, uv);
 #pragma unroll
     for (int q = 0; q < CPT; ++q) uv[q] += s[q];
+    stv<TC, CPT>(up, uv);
+  }
+}
+
+// u[rows(a)] += P_a uc[coarse(a)] with one warp per aggregate: CL lanes
+// per row (CPT columns each), 32 / CL rows per pass; the prolongator row and
+// the aggregate's coarse values are read straight from global memory (the
+// coarse rows are shared by the aggregate's rows through L1).
+template <typename TC, int K>
+__global__ void __launch_bounds__(BS) k_prolong_w(int nagg, const int* __restrict__ row_start,
+                                                  const int* __restrict__ coarse_start,
+                                                  const long long* __restrict__ blk_start,
+                                                  const TC* __restrict__ P, const TC* __restrict__ uc,
+                                                  TC* __restrict__ u, const int* __restrict__ done) {
+  if (*done) return;
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
+  const int lane = threadIdx.x & 31, cl = lane % CL;
+  const int a = blockIdx.x * NWARP + (threadIdx.x >> 5);
+  if (a >= nagg) return;  // no warp-wide collectives below
+  const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
+  const int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
+  const TC* Pa = P + __ldg(blk_start + a);
+  const TC* ucp = uc + (size_t)cs * K + cl * CPT;
+  for (int i = rs + lane / CL; i < re; i += RPW) {
+    const TC* pr = Pa + (size_t)(i - rs) * ra;
+    TC* up = u + (size_t)i * K + cl * CPT;
+    TC sv[CPT], uv[CPT];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) sv[t] = TC(0);
+    for (int p = 0; p < ra; ++p) {  // the same order as k_prolong: P_a row . uc, then added to u
+      const TC pv = __ldg(pr + p);
+      TC cv[CPT];
+      ldv<TC, CPT>(ucp + (size_t)p * K, cv);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) sv[t] = fma(pv, cv[t], sv[t]);
+    }
+    ldp<TC, CPT>(up, uv);
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) uv[t] += sv[t];
     stv<TC, CPT>(up, uv);
   }
 }
@@ -877,11 +1235,37 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
 #pragma unroll
     for (int t = 0; t < 2 * NF; ++t) sdot[t][threadIdx.x] = 0.f;
   }
-  // one row range per CTA, or (persistent launch, one system, never staged)
-  // every gridDim.x-th range
-  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  // one row range per CTA, or (persistent launch, one system) every
+  // gridDim.x-th range; float matrices are staged through the double-buffered
+  // pipeline (the next range arrives while this one is processed)
+  constexpr bool PIPE = sizeof(TC) == 4;
+  const bool piped = PIPE && sg.enabled;
+  if (piped) {
+    pipe_init(smraw);
+    if (threadIdx.x == 0 && (int)blockIdx.x < nchunk) {
+      const float* v1[1] = {reinterpret_cast<const float*>(val)};
+      pipe_issue<1>(sg, smraw, 0, cta_row[blockIdx.x], cta_row[blockIdx.x + 1], rowptr, col, v1);
+    }
+  }
+  int it = 0;
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x, ++it) {
   const int r0 = cta_row[chunk], r1 = cta_row[chunk + 1];
-  const CsrView<TC> cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
+  CsrView<TC> cv;
+  if (piped) {
+    const int nxt = chunk + gridDim.x;
+    if (threadIdx.x == 0 && nxt < nchunk) {
+      const float* v1[1] = {reinterpret_cast<const float*>(val)};
+      pipe_issue<1>(sg, smraw, (it + 1) & 1, cta_row[nxt], cta_row[nxt + 1], rowptr, col, v1);
+    }
+    const int* prp;
+    const int* pcs;
+    const float* pv[1];
+    int roff, joff;
+    pipe_wait<1>(sg, smraw, it & 1, it >> 1, r0, rowptr, prp, roff, pcs, pv, joff);
+    cv = CsrView<TC>{prp, roff, pcs, joff, reinterpret_cast<const TC*>(pv[0]), joff};
+  } else {
+    cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
+  }
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;
     bool valid = i < r1;
@@ -933,6 +1317,7 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
       stv<TC, CPT>(z + o, zt);
     }
   }
+  if (piped) __syncthreads();  // the buffer is refilled two ranges on
   }
   if (mode == 2) return;
   double dd[CPT];

@@ -106,6 +106,78 @@ template <typename TC>
 void launch_presmooth0(int K, const Level& L, const RPart& rp, const double* r, TC* u0, TC* f0,
                        const int* done, cudaStream_t st);
 
+// Grouped coarse-level kernels (columns K >= 8, at most 8 rows per group and
+// 8 coarse dofs per aggregate); the caller checks grouped_ok first.  jl lanes
+// split a group's pattern columns (1, 2 or 4, at most 32 / CL).
+inline bool grouped_ok(int K, const Level& L) { return K >= 8 && L.grp_ok && L.grp_rmax <= 8; }
+template <typename TC>
+inline bool grouped_jl_ok(int K, int jl) {
+  const int cpt = (K * (int)sizeof(TC) >= 16) ? 16 / (int)sizeof(TC) : K;
+  return (jl == 1 || jl == 2 || jl == 4) && (K / cpt) * jl <= 32;
+}
+
+template <class F>
+inline void dispatch_jl(int jl, F&& f) {
+  switch (jl) {
+    case 1: f(ic<1>{}); return;
+    case 2: f(ic<2>{}); return;
+    case 4: f(ic<4>{}); return;
+  }
+  throw Error(AMG_ERR_INVALID_ARG, "internal: unsupported group lane split");
+}
+
+template <typename TC>
+inline void launch_smooth_g(int K, int jl, const Level& L, const TC* f, const TC* u, TC* v, const int* done,
+                            cudaStream_t st) {
+  dispatch_k(K, [&](auto kc) {
+    constexpr int KK = decltype(kc)::value;
+    dispatch_jl(jl, [&](auto jc) {
+      constexpr int JL = decltype(jc)::value;
+      if constexpr (KK >= 8 && VT<TC, KK>::CL * JL <= 32) {
+        constexpr int per_cta = NWARP * (32 / (VT<TC, KK>::CL * JL));
+        const int grid = (L.ngrp + per_cta - 1) / per_cta;
+        if (L.grp_rmax <= 4)
+          k_smooth_g<TC, KK, 4, JL><<<grid, BS, 0, st>>>(L.ngrp, L.gstart, L.rowptr, L.col, vals<TC>(L),
+                                                         dinvs<TC>(L), f, u, v, done);
+        else
+          k_smooth_g<TC, KK, 8, JL><<<grid, BS, 0, st>>>(L.ngrp, L.gstart, L.rowptr, L.col, vals<TC>(L),
+                                                         dinvs<TC>(L), f, u, v, done);
+      } else {
+        throw Error(AMG_ERR_INVALID_ARG, "internal: grouped kernels need at least 8 columns");
+      }
+    });
+  });
+  AMG_LAUNCH_CHECK();
+}
+
+template <typename TC>
+inline void launch_restrict_g(int K, const Level& L, const Transfer& T, const TPart& tp, const Level& C,
+                              bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, const int* done,
+                              cudaStream_t st) {
+  dispatch_k(K, [&](auto kc) {
+    constexpr int KK = decltype(kc)::value;
+    dispatch_jl(tp.jl, [&](auto jc) {
+      constexpr int JL = decltype(jc)::value;
+      if constexpr (KK >= 8 && VT<TC, KK>::CL * JL <= 32) {
+        auto go = [&](auto ra, auto rm) {
+          constexpr int RA = decltype(ra)::value, RM = decltype(rm)::value;
+          k_restrict_g<TC, KK, RA, RM, JL><<<T.nagg, RG_WARPS * 32, 0, st>>>(
+              T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), L.gstart, T.gagg, L.rowptr,
+              L.col, vals<TC>(L), f, u, fc, smooth_next ? uc : nullptr, smooth_next ? dinvs<TC>(C) : nullptr,
+              done);
+        };
+        if (L.grp_rmax <= 4 && tp.ra_max <= 4) go(ic<4>{}, ic<4>{});
+        else if (L.grp_rmax <= 4) go(ic<4>{}, ic<8>{});
+        else if (tp.ra_max <= 4) go(ic<8>{}, ic<4>{});
+        else go(ic<8>{}, ic<8>{});
+      } else {
+        throw Error(AMG_ERR_INVALID_ARG, "internal: grouped kernels need at least 8 columns");
+      }
+    });
+  });
+  AMG_LAUNCH_CHECK();
+}
+
 // shared memory of a staged SpMV kernel reading one value array of type TC
 template <typename TC>
 inline size_t csr_stage_bytes(const Stage& sg) {
@@ -116,6 +188,10 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   template <>                                                                                          \
   void launch_smooth<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,   \
                          TC* v, const int* done, cudaStream_t st) {                                    \
+    if (nzl <= 0) { /* grouped coarse level, -nzl lanes per group column split (0: one) */            \
+      launch_smooth_g<TC>(K, nzl < 0 ? -nzl : 1, L, f, u, v, done, st);                               \
+      return;                                                                                          \
+    }                                                                                                  \
     size_t smem = csr_stage_bytes<TC>(rp.sg);                                                          \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
@@ -137,6 +213,11 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   void launch_restrict<TC>(int K, int nzl, const Level& L, const Transfer& T, const TPart& tp,         \
                            const Level& C, bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, \
                            const int* done, cudaStream_t st) {                                         \
+    if (tp.warp == 2) {                                                                                \
+      launch_restrict_g<TC>(K, L, T, tp, C, smooth_next, f, u, fc, uc, done, st);                     \
+      return;                                                                                          \
+    }                                                                                                  \
+    if (nzl <= 0) nzl = 1; /* the level is grouped; the CSR kernels take one lane group per row */    \
     if (tp.warp) {                                                                                     \
       dispatch_k(K, [&](auto kc) {                                                                     \
         constexpr int KK = decltype(kc)::value;                                                        \
@@ -178,6 +259,15 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   template <>                                                                                          \
   void launch_prolong<TC>(int K, const Transfer& T, const TPart& tp, const TC* uc, TC* u,             \
                           const int* done, cudaStream_t st) {                                          \
+    if (tp.pwarp) {                                                                                    \
+      dispatch_k(K, [&](auto kc) {                                                                     \
+        constexpr int KK = decltype(kc)::value;                                                        \
+        k_prolong_w<TC, KK><<<(T.nagg + NWARP - 1) / NWARP, BS, 0, st>>>(                              \
+            T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), uc, u, done);              \
+      });                                                                                              \
+      AMG_LAUNCH_CHECK();                                                                              \
+      return;                                                                                          \
+    }                                                                                                  \
     size_t smem = transfer_smem<TC>(tp.rows_max, tp.p_max, tp.a_max, tp.c_max, K, false);             \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
@@ -203,7 +293,8 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   void launch_post0<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,    \
                         const double* r, const float* rlo, TC* z, const KState& ks, int mode,          \
                         cudaStream_t st, int grid) {                                                   \
-    size_t smem = csr_stage_bytes<TC>(rp.sg);                                                          \
+    /* float matrices stage through the pipeline (two buffers when persistent) */                      \
+    size_t smem = sizeof(TC) == 4 ? pipe_bytes(rp.sg, 1, grid > 0 ? 2 : 1) : csr_stage_bytes<TC>(rp.sg); \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
       dispatch_nzl(K, nzl, [&](auto nc) {                                                              \

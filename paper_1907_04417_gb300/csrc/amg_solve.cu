@@ -38,20 +38,21 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
   }
 }
 
-// q = A p in double-float on the float32 pipes: A as (val32, vallo), p as
-// (ph, pl), every product and sum error-free up to the final rounding of
-// the pair; q is stored as a float pair and p.q is accumulated in
-// double-float.  The row loop is software-pipelined (the gathers of the next
-// non-zero are in flight while the current one is accumulated) and the p.q
-// accumulators live in shared memory, one slot per thread, so that four CTAs
-// fit on an SM.  Offsets into the n x K blocks are 32-bit (n K < 2^32 is
-// checked on the host).
+// q = A p in double-float on the float32 pipes: A as (val32, vallo), p a
+// float32 vector (the search direction is rounded to float32 when it is
+// formed, so every product a_ij p_j is error-free up to the final rounding
+// of the pair); q is stored as a float pair and p.q is accumulated in
+// double-float.  With one lane group per row the gathers of a whole row are
+// issued before its first product (otherwise the loop is software-pipelined
+// one non-zero ahead), and the p.q accumulators live in shared memory, one
+// slot per thread, so that three CTAs fit on an SM.  Offsets into the n x K
+// blocks are 32-bit (n K < 2^32 is checked on the host).
 template <int K, int NZL>
-__global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
-                                                   const float* __restrict__ alo, const float* __restrict__ ph,
-                                                   const float* __restrict__ pl, float* __restrict__ qh,
-                                                   float* __restrict__ ql, KState ks, Stage sg, int nchunk) {
+                                                   const float* __restrict__ alo, const float* __restrict__ p,
+                                                   float* __restrict__ qh, float* __restrict__ ql, KState ks,
+                                                   Stage sg, int nchunk) {
   if (*ks.done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
@@ -62,30 +63,35 @@ __global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_r
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
 #pragma unroll
   for (int t = 0; t < 2 * CPT; ++t) sdot[t][threadIdx.x] = 0.f;
-  // row chunks: one per CTA, or (persistent launch, never staged) every
-  // gridDim.x-th chunk
-  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  // row chunks: one per CTA, or (persistent launch) every gridDim.x-th
+  // chunk; staged launches take col, val_hi and val_lo (and rowptr) through
+  // the double-buffered pipeline, the next chunk arriving while this one is
+  // processed
+  if (sg.enabled) {
+    pipe_init(smraw);
+    if (threadIdx.x == 0 && (int)blockIdx.x < nchunk) {
+      const float* v2[2] = {ahi, alo};
+      pipe_issue<2>(sg, smraw, 0, cta_row[blockIdx.x], cta_row[blockIdx.x + 1], rowptr, col, v2);
+    }
+  }
+  int it = 0;
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x, ++it) {
   const int r0 = cta_row[chunk], r1 = cta_row[chunk + 1];
-  // stage col, val_hi and val_lo of the CTA's rows
   const int* rp = rowptr;
   const int* cc = col;
   const float* va = ahi;
   const float* vb = alo;
   int roff = 0, joff = 0;
-  {
-    const void* src[2] = {ahi, alo};
-    const int w[2] = {4, 4};
-    const void* dst[2];
-    const int *srp, *scol;
-    int j4, j8;
-    if (stage_csr<2>(sg, smraw, r0, r1, rowptr, col, src, w, dst, srp, scol, j4, j8)) {
-      rp = srp;
-      cc = scol;
-      va = static_cast<const float*>(dst[0]);
-      vb = static_cast<const float*>(dst[1]);
-      roff = r0;
-      joff = j4;
+  if (sg.enabled) {
+    const int nxt = chunk + gridDim.x;
+    if (threadIdx.x == 0 && nxt < nchunk) {
+      const float* v2[2] = {ahi, alo};
+      pipe_issue<2>(sg, smraw, (it + 1) & 1, cta_row[nxt], cta_row[nxt + 1], rowptr, col, v2);
     }
+    const float* pv[2];
+    pipe_wait<2>(sg, smraw, it & 1, it >> 1, r0, rowptr, rp, roff, cc, pv, joff);
+    va = pv[0];
+    vb = pv[1];
   }
   const unsigned lo = (unsigned)(cl * CPT);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
@@ -97,32 +103,88 @@ __global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_r
     if (valid) {
       const int j1 = rp[i + 1 - roff] - joff;
       int j = rp[i - roff] - joff + nzl;
-      if (j < j1) {
-        float a = va[j], b = vb[j];
-        float xh[CPT], xl[CPT];
-        {
-          const unsigned off = (unsigned)cc[j] * (unsigned)K + lo;
-          ldv<float, CPT>(ph + off, xh);
-          ldv<float, CPT>(pl + off, xl);
+      if constexpr (gather_depth<NZL>() != 4 && CPT % 2 == 0) {
+        // predicated batches: every gather of a batch is issued before the
+        // first product (a 9-point row in one memory round trip); the
+        // double-float steps run on column pairs
+        constexpr int U = gather_depth<NZL>(), NP = CPT / 2;
+        F2 h2[NP], l2[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) h2[q] = l2[q] = F2{0ull};
+        for (; j < j1; j += U * NZL) {
+          F2 xv[U][NP];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j + u * NZL;
+            if (jj < j1) {
+              const float* src = p + (unsigned)cc[jj] * (unsigned)K + lo;
+              if constexpr (NP == 2) {
+                const ulonglong2 t2 = __ldg(reinterpret_cast<const ulonglong2*>(src));
+                xv[u][0] = F2{t2.x};
+                xv[u][1] = F2{t2.y};
+              } else {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) xv[u][q] = F2{__ldg(reinterpret_cast<const unsigned long long*>(src) + q)};
+              }
+            } else {
+#pragma unroll
+              for (int q = 0; q < NP; ++q) xv[u][q] = F2{0ull};
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j + u * NZL;
+            const float a = jj < j1 ? va[jj] : 0.f, b = jj < j1 ? vb[jj] : 0.f;
+            const F2 a2 = f2_pack(a, a), b2 = f2_pack(b, b);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) df_acc1_x2(a2, b2, xv[u][q], h2[q], l2[q]);
+          }
         }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          f2_unpack(h2[q], sh[2 * q], sh[2 * q + 1]);
+          f2_unpack(l2[q], sl[2 * q], sl[2 * q + 1]);
+        }
+      } else if constexpr (gather_depth<NZL>() != 4) {
+        // predicated batches, scalar columns
+        constexpr int U = gather_depth<NZL>();
+        for (; j < j1; j += U * NZL) {
+          float xv[U][CPT];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j + u * NZL;
+            if (jj < j1) {
+              ldv<float, CPT>(p + (unsigned)cc[jj] * (unsigned)K + lo, xv[u]);
+            } else {
+#pragma unroll
+              for (int t = 0; t < CPT; ++t) xv[u][t] = 0.f;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j + u * NZL;
+            const float a = jj < j1 ? va[jj] : 0.f, b = jj < j1 ? vb[jj] : 0.f;
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[u][t], sh[t], sl[t]);
+          }
+        }
+      } else if (j < j1) {
+        float a = va[j], b = vb[j];
+        float xv[CPT];
+        ldv<float, CPT>(p + (unsigned)cc[j] * (unsigned)K + lo, xv);
         for (j += NZL; j < j1; j += NZL) {
           const float a2 = va[j], b2 = vb[j];
-          float yh[CPT], yl[CPT];
-          const unsigned off = (unsigned)cc[j] * (unsigned)K + lo;
-          ldv<float, CPT>(ph + off, yh);
-          ldv<float, CPT>(pl + off, yl);
+          float yv[CPT];
+          ldv<float, CPT>(p + (unsigned)cc[j] * (unsigned)K + lo, yv);
 #pragma unroll
-          for (int t = 0; t < CPT; ++t) df_acc(a, b, xh[t], xl[t], sh[t], sl[t]);
+          for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[t], sh[t], sl[t]);
 #pragma unroll
-          for (int t = 0; t < CPT; ++t) {
-            xh[t] = yh[t];
-            xl[t] = yl[t];
-          }
+          for (int t = 0; t < CPT; ++t) xv[t] = yv[t];
           a = a2;
           b = b2;
         }
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) df_acc(a, b, xh[t], xl[t], sh[t], sl[t]);
+        for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[t], sh[t], sl[t]);
       }
 #pragma unroll
       for (int t = 0; t < CPT; ++t) df_norm(sh[t], sl[t]);
@@ -138,20 +200,20 @@ __global__ void __launch_bounds__(BS, 4) k_cg_q_df(const int* __restrict__ cta_r
     }
     if (valid && nzl == 0) {
       const unsigned o = (unsigned)i * (unsigned)K + lo;
-      float hv[CPT], lv[CPT];
-      ldv<float, CPT>(ph + o, hv);
-      ldv<float, CPT>(pl + o, lv);
+      float pv[CPT];
+      ldv<float, CPT>(p + o, pv);
       stv<float, CPT>(qh + o, sh);
       stv<float, CPT>(ql + o, sl);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
         float h = sdot[t][threadIdx.x], l = sdot[CPT + t][threadIdx.x];
-        df_mac(hv[t], lv[t], sh[t], sl[t], h, l);
+        df_acc1(sh[t], sl[t], pv[t], h, l);
         sdot[t][threadIdx.x] = h;
         sdot[CPT + t][threadIdx.x] = l;
       }
     }
   }
+  if (sg.enabled) __syncthreads();  // the buffer is refilled two chunks on
   }
   double d[CPT];
 #pragma unroll
@@ -269,9 +331,8 @@ __global__ void __launch_bounds__(BS) k_cg_init(const int* __restrict__ cta_row,
   }
 }
 
-// p = z + beta p; with SPLIT, p lives as the double-float pair (ph, pl)
-// read by the double-float q = A p.
-// z is stored in the cycle precision TZ; ``first`` starts the recurrence
+// p = z + beta p in float64 (the float64 CG; the double-float CG has
+// k_cg_p_df).  z is stored in the cycle precision TZ; ``first`` starts the recurrence
 // (p = z, the previous p is not read).
 template <int K, typename TZ>
 __global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, const TZ* __restrict__ z,
@@ -355,15 +416,17 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
   finish_update<K>(ks, sm, tot);
 }
 
-// x += alpha p (with the alpha of this iteration), then p = z + beta p, on
-// double-float pairs; ``first`` starts the recurrence (p = z, x untouched).
-// After the last iteration k_cg_x_df applies the final alpha p, which this
-// kernel skips once every column has stopped.
+// x += alpha p (with the alpha of this iteration, x a double-float pair and
+// p an exact float32), then p = fl32(z + beta p); ``first`` starts the
+// recurrence (p = z, x untouched).  Rounding the search direction to float32
+// only perturbs it at the level of the float32 cycle's own rounding: x and r
+// stay consistent because q = A p is formed from the same rounded p.  After
+// the last iteration k_cg_x_df applies the final alpha p, which this kernel
+// skips once every column has stopped.
 template <int K>
 __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
-                                                float* __restrict__ ph, float* __restrict__ pl,
-                                                float* __restrict__ xh, float* __restrict__ xl, KState ks,
-                                                int first, int nchunk) {
+                                                float* __restrict__ p, float* __restrict__ xh,
+                                                float* __restrict__ xl, KState ks, int first, int nchunk) {
   if (*ks.done) return;
   constexpr int CPT = VT<float, K>::CPT;
   const int cfirst = (int)((threadIdx.x * CPT) % K);
@@ -377,33 +440,26 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
   for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
   const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
-    float zv[CPT], pa[CPT], pb[CPT];
+    float zv[CPT], pv[CPT];
     ldv<float, CPT>(z + e, zv);
     if (first) {
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) {
-        pa[t] = zv[t];
-        pb[t] = 0.f;
-      }
+      for (int t = 0; t < CPT; ++t) pv[t] = zv[t];
     } else {
       float xa[CPT], xb[CPT];
-      ldp<float, CPT>(ph + e, pa);
-      ldp<float, CPT>(pl + e, pb);
+      ldp<float, CPT>(p + e, pv);
       ldp<float, CPT>(xh + e, xa);
       ldp<float, CPT>(xl + e, xb);
 #pragma unroll
       for (int t = 0; t < CPT; ++t) {
-        df_mac(ah[t], al[t], pa[t], pb[t], xa[t], xb[t]);
-        float sh = zv[t], sl = 0.f;
-        df_mac(bh[t], bl[t], pa[t], pb[t], sh, sl);
-        pa[t] = sh;
-        pb[t] = sl;
+        df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
+        df_norm(xa[t], xb[t]);
+        pv[t] = fmaf(bl[t], pv[t], fmaf(bh[t], pv[t], zv[t]));
       }
       stv<float, CPT>(xh + e, xa);
       stv<float, CPT>(xl + e, xb);
     }
-    stv<float, CPT>(ph + e, pa);
-    stv<float, CPT>(pl + e, pb);
+    stv<float, CPT>(p + e, pv);
   }
   }
 }
@@ -411,9 +467,8 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
 // x += alpha p once after the loop (the step of the last iteration; the
 // alpha of columns that stopped earlier is already zero).
 template <int K>
-__global__ void __launch_bounds__(BS) k_cg_x_df(const int* __restrict__ cta_row, const float* __restrict__ ph,
-                                                const float* __restrict__ pl, float* __restrict__ xh,
-                                                float* __restrict__ xl, KState ks) {
+__global__ void __launch_bounds__(BS) k_cg_x_df(const int* __restrict__ cta_row, const float* __restrict__ p,
+                                                float* __restrict__ xh, float* __restrict__ xl, KState ks) {
   constexpr int CPT = VT<float, K>::CPT;
   const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
   const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
@@ -423,13 +478,15 @@ __global__ void __launch_bounds__(BS) k_cg_x_df(const int* __restrict__ cta_row,
 #pragma unroll
   for (int t = 0; t < CPT; ++t) split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
-    float pa[CPT], pb[CPT], xa[CPT], xb[CPT];
-    ldv<float, CPT>(ph + e, pa);
-    ldv<float, CPT>(pl + e, pb);
+    float pv[CPT], xa[CPT], xb[CPT];
+    ldv<float, CPT>(p + e, pv);
     ldp<float, CPT>(xh + e, xa);
     ldp<float, CPT>(xl + e, xb);
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) df_mac(ah[t], al[t], pa[t], pb[t], xa[t], xb[t]);
+    for (int t = 0; t < CPT; ++t) {
+      df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
+      df_norm(xa[t], xb[t]);
+    }
     stv<float, CPT>(xh + e, xa);
     stv<float, CPT>(xl + e, xb);
   }
@@ -534,7 +591,7 @@ struct Workspace {
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   bool split = false;  // double-float CG vectors (float32-cycle mode)
   float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr;
-  float *ph = nullptr, *pl = nullptr, *qh = nullptr, *ql = nullptr;
+  float *ph = nullptr, *qh = nullptr, *ql = nullptr;  // p is float32 (see k_cg_p_df)
   std::vector<void*> f, u, v;
   KState ks{};
   int* zero_flag = nullptr;
@@ -546,16 +603,18 @@ struct Workspace {
   int q_stage = 1;        // whether the double-float q = A p stages its matrix slice
   RPart rq{};             // level-0 row ranges of the double-float q = A p (own CTA size)
   int q_grid = 0;         // > 0: persistent q launch of q_grid CTAs over rq's ranges
-  int pers_grid = 0;      // CTAs of the persistent level-0 launches below (one system)
-  int upd_pers = 0, p_pers = 0, post_pers = 0;  // which level-0 kernels run persistent
-  KState ksf{};           // the CG state seen through the persistent launches' CTA groups
+  // persistent level-0 launches (one system): CTAs of the update, direction
+  // and post-smoother kernels, 0 for one CTA per row range
+  int upd_grid = 0, p_grid = 0, post_grid = 0;
+  int post_stage = 0;            // persistent post-smoother: staged through the pipeline
+  KState ksf_upd{}, ksf_post{};  // the CG state seen through those launches' CTA groups
   // the tuned choices, as applied (written to and read from the tuning cache)
   std::vector<long long> t_rp;  // per smoothed level: target, stage, lanes
   std::vector<int> t_rps, t_nzl;
   std::vector<int> t_tp, t_tps, t_tpw;  // per transfer: rows target (0: default), stage, warp kernel
   long long t_q = 0;                    // q: target (0: level-0 ranges), lanes, stage, persistent grid
   int t_qn = 0, t_qs = 0, t_qg = 0;
-  int t_pg = 0, t_pu = 0, t_pp = 0, t_ppost = 0;  // persistent grid and flags of update / p / post
+  int t_pu = 0, t_pp = 0, t_ppost = 0;  // persistent grids of update / p / post
   KState ksq{};           // the CG state seen through the q launch's CTA groups
   std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
   std::vector<RPart> rp;  // per level: row ranges for this column count
@@ -711,6 +770,17 @@ static int round_k(int nrhs) {
 // matter for timing).  The chosen layout serves every kernel of the level.
 static const long long kTargets[] = {256, 512, 1024, 2048, 4096, 8192};
 
+// AMG_COARSE_KERNELS in the environment overrides the tuner on grouped
+// coarse levels: "grouped" takes the grouped sweep and restriction wherever
+// the level allows them, "csr" never takes them; unset, timing decides.
+static int coarse_kernel_override() {
+  const char* e = std::getenv("AMG_COARSE_KERNELS");
+  if (!e) return 0;
+  if (std::strcmp(e, "grouped") == 0) return 1;
+  if (std::strcmp(e, "csr") == 0) return -1;
+  return 0;
+}
+
 // AMG_TUNE_LOG=1 in the environment prints every candidate timing to stderr.
 static bool tune_log() {
   static int on = -1;
@@ -747,7 +817,9 @@ static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, 
     W.tp[k] = make_tpart(W.ar, P.tr[k], P.lev[k], W.K, W.err, target);
     W.tp[k].sg.enabled = W.tp[k].sg.enabled && stage;
   }
-  W.tp[k].warp = warp;
+  W.tp[k].warp = warp % 4;         // restriction kernel
+  W.tp[k].pwarp = (warp / 4) % 2;  // prolongation kernel
+  W.tp[k].jl = 1 << (warp / 8);    // grouped restriction: lanes per group column split
   W.t_tp[k] = target;
   W.t_tps[k] = stage;
   W.t_tpw[k] = warp;
@@ -767,18 +839,26 @@ static void apply_q(Plan& P, Workspace& W, long long target, int nzl, int stage,
   W.t_qs = stage;
   W.t_qg = grid;
 }
-static void apply_persist(Workspace& W, int grid, int upd, int p, int post) {
-  if (grid > 0) {
-    W.pers_grid = grid;
-    W.ksf = view_state(W.ar, W.ks, make_flat(W.ar, grid), W.K);
-  }
-  W.upd_pers = upd;
-  W.p_pers = p;
-  W.post_pers = post;
-  W.t_pg = grid;
+static void apply_persist(Workspace& W, int upd, int p, int post) {
+  W.upd_grid = upd;
+  W.p_grid = p;
+  W.post_stage = post < 0 ? 1 : 0;  // a negative post grid: staged through the pipeline
+  if (post < 0) post = -post;
+  W.post_grid = post;
+  if (upd > 0) W.ksf_upd = view_state(W.ar, W.ks, make_flat(W.ar, upd), W.K);
+  if (post > 0) W.ksf_post = view_state(W.ar, W.ks, make_flat(W.ar, post), W.K);
   W.t_pu = upd;
   W.t_pp = p;
-  W.t_ppost = post;
+  W.t_ppost = W.post_stage ? -post : post;
+}
+
+// Streaming multiprocessors of the current device (persistent grids are
+// multiples of it).
+static int sm_count() {
+  int dev = 0, n = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  AMG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  return n > 0 ? n : 1;
 }
 
 // Tuning cache: when the environment variable AMG_TUNE_CACHE names a file,
@@ -786,7 +866,7 @@ static void apply_persist(Workspace& W, int grid, int upd, int p, int post) {
 // sweeps) has a line there takes its choices from that line instead of
 // timing them, and newly tuned choices are appended to it.
 static std::string tune_key(const Plan& P, int K, int prec, int pre, int post, bool split) {
-  std::string k = "amg-tune-1 K" + std::to_string(K) + " prec" + std::to_string(prec) + " split" +
+  std::string k = "amg-tune-2 K" + std::to_string(K) + " prec" + std::to_string(prec) + " split" +
                   std::to_string(split ? 1 : 0) + " sweeps" + std::to_string(pre) + "/" + std::to_string(post) +
                   " nsys" + std::to_string(P.nsys) + " levels";
   for (int l = 0; l < P.L; ++l) k += " " + std::to_string(P.lev[l].n) + ":" + std::to_string(P.lev[l].nnz);
@@ -840,7 +920,7 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
     Arena tmp;
     for (long long t : kTargets) {
       RPart rp0 = make_rpart(tmp, L, t, sys, W.err);
-      if (t > kTargets[0] && rp0.ncta < 152) break;  // fewer CTAs than SMs: stop growing
+      if (t > kTargets[0] && rp0.ncta < sm_count()) break;  // fewer CTAs than SMs: stop growing
       for (int stage = rp0.sg.enabled; stage >= 0; --stage)
       for (int n : nzl_candidates<TC>(K)) {
         RPart rp = rp0;
@@ -868,6 +948,34 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
     }
     AMG_CUDA(cudaDeviceSynchronize());
   }
+  const int ovr = coarse_kernel_override();
+  if (k > 0 && grouped_ok(K, L) && ovr >= 0) {  // the grouped sweep (lanes -jl, 0 for jl = 1, stand for it)
+    TC* f = static_cast<TC*>(W.f[k]);
+    TC* u = static_cast<TC*>(W.u[k]);
+    TC* v = static_cast<TC*>(W.v[k]);
+    float gbest = 1e30f;
+    int gn = 0;
+    for (int jl : {1, 2, 4}) {
+      if (!grouped_jl_ok<TC>(K, jl)) continue;
+      const int code = jl == 1 ? 0 : -jl;
+      launch_smooth<TC>(K, code, L, W.rp[k], f, u, v, W.zero_flag, 0);
+      AMG_CUDA(cudaEventRecord(e0, 0));
+      for (int r = 0; r < 3; ++r) launch_smooth<TC>(K, code, L, W.rp[k], f, u, v, W.zero_flag, 0);
+      AMG_CUDA(cudaEventRecord(e1, 0));
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (tune_log()) fprintf(stderr, "[tune] level %d K %d smooth grouped jl %d: %.1f us\n", k, K, jl, ms * 1e3 / 3);
+      if (ms < gbest) {
+        gbest = ms;
+        gn = code;
+      }
+    }
+    if (gbest < best || ovr > 0) {
+      best = gbest;
+      bn = gn;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   apply_level(P, W, k, bt, bs, bn);
@@ -886,7 +994,7 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     Arena tmp;
     for (int t : {32, 64, 128, 256, 512}) {
       TPart tp0 = make_tpart(tmp, P.tr[k], P.lev[k], K, W.err, t);
-      if (t > 32 && tp0.ncta < 152) break;
+      if (t > 32 && tp0.ncta < sm_count()) break;
       for (int stage = tp0.sg.enabled; stage >= 0; --stage) {
         TPart tp = tp0;
         tp.sg.enabled = stage;
@@ -936,10 +1044,69 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     if (tune_log()) fprintf(stderr, "[tune] level %d K %d restrict warp-per-aggregate: %.1f us\n", k, K, ms * 1e3 / 3);
     warp_best = ms < best;
+    if (warp_best) best = ms;
+  }
+  // the grouped restriction (one CTA per aggregate) out of a grouped level
+  bool grp_best = false;
+  int gjl = 1;
+  const int ovr = coarse_kernel_override();
+  if (k > 0 && grouped_ok(K, P.lev[k]) && P.tr[k].gagg && W.tp[k].ra_max <= 8 && ovr >= 0) {
+    float gbest = 1e30f;
+    for (int jl : {1, 2, 4}) {
+      if (!grouped_jl_ok<TC>(K, jl)) continue;
+      TPart tg = W.tp[k];
+      tg.warp = 2;
+      tg.jl = jl;
+      auto run = [&] {
+        launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], tg, P.lev[k + 1], k + 1 < P.L - 1,
+                            static_cast<TC*>(W.f[k]), static_cast<TC*>(W.u[k]), static_cast<TC*>(W.f[k + 1]),
+                            static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
+      };
+      run();
+      AMG_CUDA(cudaEventRecord(e0, 0));
+      for (int r = 0; r < 3; ++r) run();
+      AMG_CUDA(cudaEventRecord(e1, 0));
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (tune_log()) fprintf(stderr, "[tune] level %d K %d restrict grouped jl %d: %.1f us\n", k, K, jl, ms * 1e3 / 3);
+      if (ms < gbest) {
+        gbest = ms;
+        gjl = jl;
+      }
+    }
+    grp_best = gbest < best || ovr > 0;
+  }
+  // prolongation: CTA ranges of the chosen partition against one warp per aggregate
+  int pw = 0;
+  {
+    Arena tmp;
+    TPart tp = bt > 0 ? make_tpart(tmp, P.tr[k], P.lev[k], K, W.err, bt) : W.tp[k];
+    float pbest = 1e30f;
+    for (int w : {0, 1}) {
+      tp.pwarp = w;
+      auto run = [&] {
+        launch_prolong<TC>(K, P.tr[k], tp, static_cast<TC*>(W.v[k + 1]), static_cast<TC*>(W.u[k]), W.zero_flag, 0);
+      };
+      run();
+      AMG_CUDA(cudaEventRecord(e0, 0));
+      for (int r = 0; r < 3; ++r) run();
+      AMG_CUDA(cudaEventRecord(e1, 0));
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (tune_log()) fprintf(stderr, "[tune] level %d K %d prolong warp %d: %.1f us\n", k, K, w, ms * 1e3 / 3);
+      if (ms < pbest) {
+        pbest = ms;
+        pw = w;
+      }
+    }
+    AMG_CUDA(cudaDeviceSynchronize());
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  apply_transfer(P, W, k, bt, bs, warp_best ? 1 : 0);
+  const int jsel = gjl == 4 ? 2 : (gjl == 2 ? 1 : 0);
+  apply_transfer(P, W, k, bt, bs, (grp_best ? 2 : (warp_best ? 1 : 0)) + 4 * pw + 8 * jsel);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
@@ -1001,7 +1168,7 @@ static void tune_q(Plan& P, Workspace& W) {
     const KState keep_ks = W.ksq;
     for (long long t : qTargets) {
       RPart rp = make_rpart(tmp, P.lev[0], t, P.h_sys_row, W.err);
-      if (t > qTargets[0] && rp.ncta < 4 * 152) break;  // under one wave of four CTAs per SM
+      if (t > qTargets[0] && rp.ncta < 3 * sm_count()) break;  // under one wave of three CTAs per SM
       W.rq = rp;
       W.ksq = view_state(tmp, W.ks, rp, W.K);
       for (int stage = rp.sg.enabled; stage >= 0; --stage)
@@ -1018,11 +1185,12 @@ static void tune_q(Plan& P, Workspace& W) {
         }
       AMG_CUDA(cudaDeviceSynchronize());
     }
-    // persistent launches (one system): 3 or 4 CTAs per SM walk the chunks
+    // persistent launches (one system): 2 to 4 CTAs per SM walk the chunks,
+    // unstaged or through the double-buffered staging pipeline
     int bg = 0;
     if (P.nsys == 1) {
-      for (int per_sm : {4, 3}) {
-        const int grid = per_sm * 152;
+      for (int per_sm : {4, 3, 2}) {
+        const int grid = per_sm * sm_count();
         RPart flat = make_flat(tmp, grid);
         for (long long t : qTargets) {
           RPart rp = make_rpart(tmp, P.lev[0], t, P.h_sys_row, W.err);
@@ -1030,18 +1198,19 @@ static void tune_q(Plan& P, Workspace& W) {
           W.rq = rp;
           W.q_grid = grid;
           W.ksq = view_state(tmp, W.ks, flat, W.K);
-          for (int n : cand) {
-            W.nzl_q = n;
-            W.q_stage = 0;
-            float ms = time_q("df persistent", t, n, 0);
-            if (ms < best) {
-              best = ms;
-              bn = n;
-              bs = 0;
-              bt = t;
-              bg = grid;
+          for (int stage = rp.sg.enabled; stage >= 0; --stage)
+            for (int n : cand) {
+              W.nzl_q = n;
+              W.q_stage = stage;
+              float ms = time_q("df persistent", t, n, stage);
+              if (ms < best) {
+                best = ms;
+                bn = n;
+                bs = stage;
+                bt = t;
+                bg = grid;
+              }
             }
-          }
           AMG_CUDA(cudaDeviceSynchronize());
         }
       }
@@ -1058,21 +1227,19 @@ static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st);
 static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, cudaStream_t st);
 
 // Level-0 kernels of the double-float CG (one system): each runs either one
-// CTA per row range or persistent (four CTAs per SM walking the ranges, one
-// reduction per CTA), whichever the timing favours.  The timing runs use a
-// private all-stopped flag, cleared before every launch, so that the stopping
-// test of a reducing kernel cannot turn the following launches into no-ops.
+// CTA per row range or persistent (2 to 8 CTAs per SM walking the ranges,
+// one reduction per CTA), whichever the timing favours; each kernel gets its
+// own grid.  The timing runs use a private all-stopped flag, cleared before
+// every launch, so that the stopping test of a reducing kernel cannot turn
+// the following launches into no-ops.
 static void tune_persist(Plan& P, Workspace& W) {
-  const int K = W.K;
-  apply_persist(W, 4 * 152, 0, 0, 0);
+  const int K = W.K, nsm = sm_count();
   int* tdone = W.ar.alloc<int>(1);
   int* keep_done = W.ks.done;
-  W.ks.done = tdone;
-  W.ksf.done = tdone;
   cudaEvent_t e0, e1;
   AMG_CUDA(cudaEventCreate(&e0));
   AMG_CUDA(cudaEventCreate(&e1));
-  auto timeit = [&](const char* what, int pers, auto launch) {
+  auto timeit = [&](const char* what, int grid, auto launch) {
     AMG_CUDA(cudaMemsetAsync(tdone, 0, sizeof(int), 0));
     launch();
     AMG_CUDA(cudaEventRecord(e0, 0));
@@ -1084,32 +1251,155 @@ static void tune_persist(Plan& P, Workspace& W) {
     AMG_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (tune_log()) fprintf(stderr, "[tune] %s K %d persistent %d: %.1f us\n", what, K, pers, ms * 1e3 / 3);
+    if (tune_log()) fprintf(stderr, "[tune] %s K %d persistent grid %d: %.1f us\n", what, K, grid, ms * 1e3 / 3);
     return ms;
   };
-  auto pick = [&](const char* what, int& flag, auto launch) {
-    flag = 0;
-    float a = timeit(what, 0, launch);
-    flag = 1;
-    float b = timeit(what, 1, launch);
-    flag = b < a ? 1 : 0;
+  // grid 0 (one CTA per range) against persistent grids of per_sm CTAs per
+  // SM; ``view`` receives the CG state seen through the grid's CTA groups
+  // (made before the timed launches)
+  Arena tmp;
+  KState view{};
+  auto pick = [&](const char* what, int& grid, bool reduces, auto launch) {
+    auto prepare = [&](int g) {
+      view = (g > 0 && reduces) ? view_state(tmp, W.ks, make_flat(tmp, g), K) : W.ks;
+      view.done = tdone;
+      AMG_CUDA(cudaDeviceSynchronize());
+    };
+    grid = 0;
+    prepare(0);
+    float best = timeit(what, 0, launch);
+    int bg = 0;
+    for (int per_sm : {2, 3, 4, 6, 8}) {
+      grid = per_sm * nsm;
+      if (grid * 2 > W.rp[0].ncta) break;
+      prepare(grid);
+      float ms = timeit(what, grid, launch);
+      if (ms < best) {
+        best = ms;
+        bg = grid;
+      }
+    }
+    grid = bg;
   };
-  pick("update", W.upd_pers, [&] { launch_update_df(W, P.lev[0], 0); });
-  pick("p", W.p_pers, [&] { launch_cg_p(P, W, P.lev[0], 0, 0); });
-  pick("post", W.post_pers, [&] {
-    RPart rp0 = W.rp[0];
-    if (W.post_pers) rp0.sg.enabled = 0;
-    launch_post0<float>(K, W.nzl[0], P.lev[0], rp0, static_cast<float*>(W.f[0]), static_cast<float*>(W.u[0]),
-                        W.r, W.rl, reinterpret_cast<float*>(W.z), W.post_pers ? W.ksf : W.ks, 1, 0,
-                        W.post_pers ? W.pers_grid : 0);
+  pick("update", W.upd_grid, true, [&] {
+    W.ksf_upd = view;
+    KState keep = W.ks;
+    W.ks.done = tdone;
+    launch_update_df(W, P.lev[0], 0);
+    W.ks = keep;
   });
+  pick("p", W.p_grid, false, [&] {
+    KState keep = W.ks;
+    W.ks.done = tdone;
+    launch_cg_p(P, W, P.lev[0], 0, 0);
+    W.ks = keep;
+  });
+  // post-smoother: persistent grids unstaged (code grid) and staged (code -grid)
+  int post_code = 0;
+  {
+    float pbest = 1e30f;
+    std::vector<int> codes{0};
+    for (int per_sm : {2, 3, 4, 6, 8}) {
+      const int g = per_sm * nsm;
+      if (g * 2 > W.rp[0].ncta) break;
+      codes.push_back(g);
+      if (W.rp[0].sg.enabled) codes.push_back(-g);
+    }
+    for (int code : codes) {
+      const int g = code < 0 ? -code : code;
+      view = g > 0 ? view_state(tmp, W.ks, make_flat(tmp, g), K) : W.ks;
+      view.done = tdone;
+      AMG_CUDA(cudaDeviceSynchronize());
+      RPart rp0 = W.rp[0];
+      if (code > 0) rp0.sg.enabled = 0;
+      float ms = timeit("post", code, [&] {
+        launch_post0<float>(K, W.nzl[0], P.lev[0], rp0, static_cast<float*>(W.f[0]), static_cast<float*>(W.u[0]),
+                            W.r, W.rl, reinterpret_cast<float*>(W.z), view, 1, 0, g);
+      });
+      if (ms < pbest) {
+        pbest = ms;
+        post_code = code;
+      }
+    }
+  }
+  W.post_grid = post_code < 0 ? -post_code : post_code;
+  W.post_stage = post_code < 0 ? 1 : 0;
   AMG_CUDA(cudaDeviceSynchronize());
   W.ks.done = keep_done;
-  W.ksf.done = keep_done;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  apply_persist(W, 0, W.upd_pers, W.p_pers, W.post_pers);
-  W.t_pg = W.pers_grid;
+  apply_persist(W, W.upd_grid, W.p_grid, W.post_stage ? -W.post_grid : W.post_grid);
+}
+
+// Row groups of the coarse levels (see the grouped kernels): the host
+// checks that the rows of each aggregate's coarse dofs have equal lengths and
+// consecutive storage, a kernel checks that they have the same columns, and
+// each transfer out of a grouped level gets the first group of every
+// aggregate.  Levels that fail a check keep the CSR kernels only.
+__global__ void k_check_groups(int ngrp, const int* __restrict__ gstart, const int* __restrict__ rowptr,
+                               const int* __restrict__ col, int* __restrict__ bad) {
+  const int g = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (g >= ngrp) return;
+  const int r0 = gstart[g], r1 = gstart[g + 1];
+  const int b0 = rowptr[r0], S = rowptr[r0 + 1] - b0;
+  for (int r = r0 + 1; r < r1; ++r) {
+    const int br = rowptr[r];
+    for (int j = lane; j < S; j += 32)
+      if (col[br + j] != col[b0 + j]) atomicOr(bad, 1);
+  }
+}
+
+static void ensure_groups(Plan& P) {
+  if (P.groups_done) return;
+  P.groups_done = true;
+  int* bad = P.arena->alloc<int>(1);
+  for (int k = 1; k < P.L; ++k) {
+    Level& L = P.lev[k];
+    const Transfer& T = P.tr[k - 1];
+    const std::vector<int>& gs = T.h_coarse_start;
+    if ((int)gs.size() != T.nagg + 1 || gs.back() != L.n || (int)L.h_rowptr.size() != L.n + 1) continue;
+    bool ok = true;
+    int rmax = 0;
+    for (int g = 0; g < T.nagg && ok; ++g) {
+      const int r0 = gs[g], r1 = gs[g + 1];
+      if (r1 <= r0) {
+        ok = false;
+        break;
+      }
+      rmax = std::max(rmax, r1 - r0);
+      const long long S = (long long)L.h_rowptr[r0 + 1] - L.h_rowptr[r0];
+      for (int r = r0 + 1; r < r1 && ok; ++r)
+        if ((long long)L.h_rowptr[r + 1] - L.h_rowptr[r] != S) ok = false;
+    }
+    if (!ok) continue;
+    AMG_CUDA(cudaMemset(bad, 0, sizeof(int)));
+    k_check_groups<<<(T.nagg + 7) / 8, 256>>>(T.nagg, T.coarse_start, L.rowptr, L.col, bad);
+    AMG_LAUNCH_CHECK();
+    int hbad = 0;
+    AMG_CUDA(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hbad) continue;
+    L.grp_ok = 1;
+    L.ngrp = T.nagg;
+    L.grp_rmax = rmax;
+    L.gstart = T.coarse_start;
+  }
+  for (int k = 1; k + 1 < P.L; ++k) {
+    if (!P.lev[k].grp_ok) continue;
+    const std::vector<int>& gs = P.tr[k - 1].h_coarse_start;
+    const std::vector<int>& rs = P.tr[k].h_row_start;
+    std::vector<int> ga(rs.size());
+    size_t g = 0;
+    bool ok = true;
+    for (size_t a = 0; a < rs.size() && ok; ++a) {
+      while (g < gs.size() && gs[g] < rs[a]) ++g;
+      if (g == gs.size() || gs[g] != rs[a]) ok = false;
+      else ga[a] = (int)g;
+    }
+    if (!ok) continue;
+    int* d = P.arena->alloc<int>(ga.size());
+    AMG_CUDA(cudaMemcpy(d, ga.data(), ga.size() * sizeof(int), cudaMemcpyHostToDevice));
+    P.tr[k].gagg = d;
+  }
 }
 
 static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false) {
@@ -1117,6 +1407,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
                   ((long long)pre << 8) | post;
   auto it = P.ws.find(key);
   if (it != P.ws.end()) return *it->second;
+  ensure_groups(P);
   auto W = std::make_shared<Workspace>();
   W->K = K;
   W->prec = prec;
@@ -1131,7 +1422,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   W->r = ar.alloc<double>(n0k);
   W->split = split;
   if (split) {
-    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->pl, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
+    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
   } else {
     W->p = ar.alloc<double>(n0k);
   }
@@ -1220,7 +1511,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     t += 3 * nt;
     if (t[0] > 0 || t[1] > 0) apply_q(P, *W, t[0], (int)t[1], (int)t[2], (int)t[3]);
     t += 4;
-    if (split && P.nsys == 1) apply_persist(*W, (int)t[0], (int)t[1], (int)t[2], (int)t[3]);
+    if (split && P.nsys == 1) apply_persist(*W, (int)t[0], (int)t[1], (int)t[2]);
   } else if (autotune) {
     for (int k = 0; k + 1 < P.L; ++k) {
       if (prec == 64) tune_transfer<double>(P, *W, k);
@@ -1232,7 +1523,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_rp[k], W->t_rps[k], W->t_nzl[k]});
     for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_tp[k], W->t_tps[k], W->t_tpw[k]});
     out.insert(out.end(), {W->t_q, W->t_qn, W->t_qs, W->t_qg});
-    out.insert(out.end(), {W->t_pg, W->t_pu, W->t_pp, W->t_ppost});
+    out.insert(out.end(), {(long long)W->t_pu, (long long)W->t_pp, (long long)W->t_ppost, 0LL});
     tune_cache_store(tkey, out);
   }
   P.ws[key] = W;
@@ -1328,11 +1619,11 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     res = cur[k];
   }
   TimedLaunch tl(h, AMG_KERNEL_SMOOTH_L0, st, pool);
-  const bool pers = W.post_pers && &ks == &W.ks;
+  const bool pers = W.post_grid > 0 && &ks == &W.ks;
   RPart rp0 = W.rp[0];
-  if (pers) rp0.sg.enabled = 0;
+  if (pers && !W.post_stage) rp0.sg.enabled = 0;
   launch_post0<TC>(K, W.nzl[0], P.lev[0], rp0, F(0), cur[0], W.r, W.split ? W.rl : nullptr,
-                   reinterpret_cast<TC*>(W.z), pers ? W.ksf : ks, mode, st, pers ? W.pers_grid : 0);
+                   reinterpret_cast<TC*>(W.z), pers ? W.ksf_post : ks, mode, st, pers ? W.post_grid : 0);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
@@ -1344,11 +1635,11 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
         if constexpr (VT<float, KK>::CL * NZ <= 32) {
           auto kern = k_cg_q_df<KK, NZ>;
           Stage sg = W.rq.sg;
-          sg.enabled = sg.enabled && W.q_stage && W.q_grid == 0;
-          size_t smem = stage_bytes(sg, 2, 0);
+          sg.enabled = sg.enabled && W.q_stage;
+          size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
           ensure_smem(kern, smem);
           const int grid = W.q_grid > 0 ? W.q_grid : W.rq.ncta;
-          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.pl, W.qh, W.ql,
+          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.qh, W.ql,
                                        W.ksq, sg, W.rq.ncta);
         }
       });
@@ -1395,8 +1686,8 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     if (W.split)
-      k_cg_p_df<KK><<<W.p_pers ? W.pers_grid : W.rp[0].ncta, BS, 0, st>>>(
-          W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph, W.pl, W.xh, W.xl, W.ks, first, W.rp[0].ncta);
+      k_cg_p_df<KK><<<W.p_grid ? W.p_grid : W.rp[0].ncta, BS, 0, st>>>(
+          W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph, W.xh, W.xl, W.ks, first, W.rp[0].ncta);
     else if (z_is_f32(P, W))
       k_cg_p<KK, float><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.p,
                                                      W.ks, first);
@@ -1409,9 +1700,9 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
 static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
-    k_cg_update_df<KK><<<W.upd_pers ? W.pers_grid : W.rp[0].ncta, BS, 0, st>>>(
+    k_cg_update_df<KK><<<W.upd_grid ? W.upd_grid : W.rp[0].ncta, BS, 0, st>>>(
         W.rp[0].cta_row, W.rh, W.rl, W.qh, W.ql, L.dinv32, static_cast<float*>(W.u[0]),
-        W.upd_pers ? W.ksf : W.ks, W.rp[0].ncta);
+        W.upd_grid ? W.ksf_upd : W.ks, W.rp[0].ncta);
   });
   AMG_LAUNCH_CHECK();
 }
@@ -1622,7 +1913,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   const int K = round_k(maxr);
   const bool split = o.cycle_precision == 32 && !o.outer_fp64 && P.L > 1;
   Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, split, o.autotune != 0);
-  for (KState* v : {&W.ks, &W.ksq, &W.ksf}) {  // the state and its views over other CTA groups
+  for (KState* v : {&W.ks, &W.ksq, &W.ksf_upd, &W.ksf_post}) {  // the state and its views over other CTA groups
     v->rtol = o.rtol;
     v->maxit = o.maxit;
   }
@@ -1636,7 +1927,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   if (W.split) {
     dispatch_k(K, [&](auto kc) {
       constexpr int KK = decltype(kc)::value;
-      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.ph, W.pl, W.xh, W.xl, W.ks);
+      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.ph, W.xh, W.xl, W.ks);
     });
     AMG_LAUNCH_CHECK();
     launch_pair(false, (long long)W.n0 * K, nullptr, W.xh, W.xl, W.x, nullptr, st);
