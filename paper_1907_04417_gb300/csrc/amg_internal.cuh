@@ -70,6 +70,16 @@ struct Arena {
 };
 
 // ------------------------------------------------------------ hierarchy --
+// Capacities of the shared-memory staging of a CTA's CSR slice (see
+// stage_csr in amg_kernels.cuh).
+struct Stage {
+  int rows_max = 0;  // largest row count of a CTA
+  int span4 = 0;     // capacity of the 4-byte arrays (elements, multiple of 4)
+  int span8 = 0;     // capacity of the 8-byte arrays (elements, multiple of 2)
+  int enabled = 0;   // 0: the level is read straight from global memory
+  int* err = nullptr;
+};
+
 // Every level is numbered so that each aggregate of the next level owns a
 // contiguous range of rows; the prolongator of an aggregate is then a dense
 // n_a x r_a block applied to a contiguous slice.
@@ -91,6 +101,7 @@ struct Level {
   // the coarse_start of the transfer that made the level
   int grp_ok = 0, ngrp = 0, grp_rmax = 0;
   const int* gstart = nullptr;
+  Stage gsg;  // staging of the grouped sweep's CTAs (GROUPS_PER_CTA groups each)
 };
 
 // P^{k+1}: maps level k+1 (coarse) to level k (fine).
@@ -105,16 +116,7 @@ struct Transfer {
   std::vector<int> h_row_start, h_coarse_start;
   std::vector<long long> h_blk_start;
   int* gagg = nullptr;  // nagg + 1: first row group of the fine level in each aggregate (grouped fine levels)
-};
-
-// Capacities of the shared-memory staging of a CTA's CSR slice (see
-// stage_csr in amg_kernels.cuh).
-struct Stage {
-  int rows_max = 0;  // largest row count of a CTA
-  int span4 = 0;     // capacity of the 4-byte arrays (elements, multiple of 4)
-  int span8 = 0;     // capacity of the 8-byte arrays (elements, multiple of 2)
-  int enabled = 0;   // 0: the level is read straight from global memory
-  int* err = nullptr;
+  Stage gsg;            // staging of the grouped restriction (one CTA per aggregate)
 };
 
 // Aggregate-aligned CTA ranges of one transfer for a given column count, with

@@ -805,26 +805,51 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
 // group: CL lanes split the K columns (CPT each), JL lanes split the S
 // pattern columns (lane jl takes j = jl, jl + JL, ...) and are combined by
 // shuffles; there are 32 / (CL JL) slots per warp.
-constexpr int GATHER_G = 10;  // gathers in flight per lane in the grouped kernels
+constexpr int GATHER_G = 10;   // gathers in flight per lane in the grouped kernels
+constexpr int GROUPS_PER_CTA = 32;  // row groups of one grouped-sweep CTA
+
+// A CTA's row groups cover one contiguous row range and hence one
+// contiguous non-zero range; with float values the CTA stages that slice
+// (rowptr, col, values) into shared memory with bulk TMA copies first, so the
+// gathers of u wait on nothing but themselves.
+template <typename TC>
+__device__ __forceinline__ CsrView<TC> group_view(const Stage& sg, unsigned char* smem, int r0, int r1,
+                                                  const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                  const TC* __restrict__ val) {
+  if constexpr (sizeof(TC) == 4) {
+    if (sg.enabled) {
+      pipe_init(smem);
+      if (threadIdx.x == 0) {
+        const float* v1[1] = {reinterpret_cast<const float*>(val)};
+        pipe_issue<1>(sg, smem, 0, r0, r1, rowptr, col, v1);
+      }
+      const int* rp;
+      const int* cs;
+      const float* vs[1];
+      int roff, joff;
+      pipe_wait<1>(sg, smem, 0, 0, r0, rowptr, rp, roff, cs, vs, joff);
+      return CsrView<TC>{rp, roff, cs, joff, reinterpret_cast<const TC*>(vs[0]), joff};
+    }
+  }
+  return CsrView<TC>{rowptr, 0, col, 0, val, 0};
+}
 
 template <typename TC, int K, int RA, int JL>
-__device__ __forceinline__ void group_acc(int r0, int ra, const int* __restrict__ rowptr,
-                                          const int* __restrict__ col, const TC* __restrict__ val,
-                                          const TC* __restrict__ x, int cl, int jl,
-                                          TC (&acc)[RA][VT<TC, K>::CPT]) {
+__device__ __forceinline__ void group_acc(int r0, int ra, const CsrView<TC>& cv, const TC* __restrict__ x, int cl,
+                                          int jl, TC (&acc)[RA][VT<TC, K>::CPT]) {
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, U = GATHER_G;
 #pragma unroll
   for (int p = 0; p < RA; ++p)
 #pragma unroll
     for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
-  const int base = __ldg(rowptr + r0), S = __ldg(rowptr + r0 + 1) - base;
+  const int base = cv.rp[r0 - cv.roff], S = cv.rp[r0 + 1 - cv.roff] - base;
   for (int j = jl; j < S; j += U * JL) {
     TC xv[U][CPT];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int jj = j + u * JL;
       if (jj < S) {
-        ldv<TC, CPT>(x + (size_t)__ldg(col + base + jj) * K + cl * CPT, xv[u]);
+        ldv<TC, CPT>(x + (size_t)cv.col[base + jj - cv.coff] * K + cl * CPT, xv[u]);
       } else {
 #pragma unroll
         for (int t = 0; t < CPT; ++t) xv[u][t] = TC(0);
@@ -833,11 +858,11 @@ __device__ __forceinline__ void group_acc(int r0, int ra, const int* __restrict_
 #pragma unroll
     for (int p = 0; p < RA; ++p) {
       if (p < ra) {
-        const TC* vp = val + base + (size_t)p * S;
+        const TC* vp = cv.val + base + (size_t)p * S - cv.voff;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int jj = j + u * JL;
-          const TC a = jj < S ? __ldg(vp + jj) : TC(0);
+          const TC a = jj < S ? vp[jj] : TC(0);
 #pragma unroll
           for (int t = 0; t < CPT; ++t) acc[p][t] = fma(a, xv[u][t], acc[p][t]);
         }
@@ -854,35 +879,44 @@ __device__ __forceinline__ void group_acc(int r0, int ra, const int* __restrict_
   }
 }
 
-// v = u + D^{-1} (f - A u) on a grouped level (one l1-Jacobi sweep).
+// v = u + D^{-1} (f - A u) on a grouped level (one l1-Jacobi sweep); a CTA
+// takes GROUPS_PER_CTA consecutive groups, its slots walking them in turn.
 template <typename TC, int K, int RA, int JL>
 __global__ void __launch_bounds__(BS) k_smooth_g(int ngrp, const int* __restrict__ gstart,
                                                  const int* __restrict__ rowptr, const int* __restrict__ col,
                                                  const TC* __restrict__ val, const TC* __restrict__ dinv,
                                                  const TC* __restrict__ f, const TC* __restrict__ u,
-                                                 TC* __restrict__ v, const int* __restrict__ done) {
+                                                 TC* __restrict__ v, const int* __restrict__ done, Stage sg) {
   if (*done) return;
-  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, SPW = 32 / (CL * JL);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, SPW = 32 / (CL * JL), NSLOT = NWARP * SPW;
   const int lane = threadIdx.x & 31, cl = lane % CL, jl = (lane / CL) % JL;
-  const int g = (blockIdx.x * NWARP + (threadIdx.x >> 5)) * SPW + lane / (CL * JL);
-  // a slot past the last group computes nothing but stays for the shuffles
-  const bool live = g < ngrp;
-  const int r0 = live ? __ldg(gstart + g) : 0, ra = live ? __ldg(gstart + g + 1) - r0 : 0;
-  TC acc[RA][CPT];
-  if (live || JL > 1) group_acc<TC, K, RA, JL>(r0, live ? ra : 0, rowptr, col, val, u, cl, live ? jl : 1 << 30, acc);
-  if (!live || jl != 0) return;
+  const int slot = (threadIdx.x >> 5) * SPW + lane / (CL * JL);
+  const int ga = blockIdx.x * GROUPS_PER_CTA, gb = min(ga + GROUPS_PER_CTA, ngrp);
+  const CsrView<TC> cv = group_view<TC>(sg, smraw, __ldg(gstart + ga), __ldg(gstart + gb), rowptr, col, val);
+  // every slot runs the same number of passes (the shuffles inside
+  // group_acc need the whole warp); a slot without a group adds nothing
+  const int passes = (gb - ga + NSLOT - 1) / NSLOT;
+  for (int ps = 0; ps < passes; ++ps) {
+    const int g = ga + ps * NSLOT + slot;
+    const bool live = g < gb;
+    const int r0 = live ? __ldg(gstart + g) : __ldg(gstart + ga), ra = live ? __ldg(gstart + g + 1) - r0 : 0;
+    TC acc[RA][CPT];
+    group_acc<TC, K, RA, JL>(r0, ra, cv, u, cl, live ? jl : 1 << 30, acc);
+    if (!live || jl != 0) continue;
 #pragma unroll
-  for (int p = 0; p < RA; ++p) {
-    if (p < ra) {
-      const int i = r0 + p;
-      const size_t o = (size_t)i * K + cl * CPT;
-      TC fv[CPT], uv[CPT], out[CPT];
-      ldv<TC, CPT>(f + o, fv);
-      ldv<TC, CPT>(u + o, uv);
-      const TC di = __ldg(dinv + i);
+    for (int p = 0; p < RA; ++p) {
+      if (p < ra) {
+        const int i = r0 + p;
+        const size_t o = (size_t)i * K + cl * CPT;
+        TC fv[CPT], uv[CPT], out[CPT];
+        ldv<TC, CPT>(f + o, fv);
+        ldv<TC, CPT>(u + o, uv);
+        const TC di = __ldg(dinv + i);
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[p][t], uv[t]);
-      stv<TC, CPT>(v + o, out);
+        for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[p][t], uv[t]);
+        stv<TC, CPT>(v + o, out);
+      }
     }
   }
 }
@@ -900,8 +934,9 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_restrict_g(
     const long long* __restrict__ blk_start, const TC* __restrict__ P, const int* __restrict__ gstart,
     const int* __restrict__ gagg, const int* __restrict__ rowptr, const int* __restrict__ col,
     const TC* __restrict__ val, const TC* __restrict__ f, const TC* __restrict__ u, TC* __restrict__ fc,
-    TC* __restrict__ uc, const TC* __restrict__ dinvc, const int* __restrict__ done) {
+    TC* __restrict__ uc, const TC* __restrict__ dinvc, const int* __restrict__ done, Stage sg) {
   if (*done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, SPW = 32 / (CL * JL), NSLOT = RG_WARPS * SPW;
   __shared__ TC red[RG_WARPS][RMAX][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, cl = lane % CL, jl = (lane / CL) % JL;
@@ -909,6 +944,7 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_restrict_g(
   const int a = blockIdx.x;
   const int rs = __ldg(row_start + a), cs = __ldg(coarse_start + a), rc = __ldg(coarse_start + a + 1) - cs;
   const TC* Pa = P + __ldg(blk_start + a);
+  const CsrView<TC> cv = group_view<TC>(sg, smraw, rs, __ldg(row_start + a + 1), rowptr, col, val);
   TC accp[RMAX][CPT];
 #pragma unroll
   for (int q = 0; q < RMAX; ++q)
@@ -921,9 +957,9 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_restrict_g(
   for (int ps = 0; ps < passes; ++ps) {
     const int g = g0 + ps * NSLOT + slot;
     const bool live = g < g1;
-    const int r0 = live ? __ldg(gstart + g) : 0, ra = live ? __ldg(gstart + g + 1) - r0 : 0;
+    const int r0 = live ? __ldg(gstart + g) : rs, ra = live ? __ldg(gstart + g + 1) - r0 : 0;
     TC acc[RA][CPT];
-    group_acc<TC, K, RA, JL>(r0, ra, rowptr, col, val, u, cl, live ? jl : 1 << 30, acc);
+    group_acc<TC, K, RA, JL>(r0, ra, cv, u, cl, live ? jl : 1 << 30, acc);
     if (jl == 0) {
 #pragma unroll
       for (int p = 0; p < RA; ++p) {

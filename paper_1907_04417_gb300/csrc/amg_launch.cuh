@@ -128,20 +128,24 @@ inline void dispatch_jl(int jl, F&& f) {
 
 template <typename TC>
 inline void launch_smooth_g(int K, int jl, const Level& L, const TC* f, const TC* u, TC* v, const int* done,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* err) {
+  Stage sg = L.gsg;
+  sg.err = err;
+  if (sizeof(TC) != 4) sg.enabled = 0;
+  const size_t smem = pipe_bytes(sg, 1, 1);
   dispatch_k(K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     dispatch_jl(jl, [&](auto jc) {
       constexpr int JL = decltype(jc)::value;
       if constexpr (KK >= 8 && VT<TC, KK>::CL * JL <= 32) {
-        constexpr int per_cta = NWARP * (32 / (VT<TC, KK>::CL * JL));
-        const int grid = (L.ngrp + per_cta - 1) / per_cta;
-        if (L.grp_rmax <= 4)
-          k_smooth_g<TC, KK, 4, JL><<<grid, BS, 0, st>>>(L.ngrp, L.gstart, L.rowptr, L.col, vals<TC>(L),
-                                                         dinvs<TC>(L), f, u, v, done);
-        else
-          k_smooth_g<TC, KK, 8, JL><<<grid, BS, 0, st>>>(L.ngrp, L.gstart, L.rowptr, L.col, vals<TC>(L),
-                                                         dinvs<TC>(L), f, u, v, done);
+        const int grid = (L.ngrp + GROUPS_PER_CTA - 1) / GROUPS_PER_CTA;
+        auto go = [&](auto kern) {
+          ensure_smem(kern, smem);
+          kern<<<grid, BS, smem, st>>>(L.ngrp, L.gstart, L.rowptr, L.col, vals<TC>(L), dinvs<TC>(L), f, u, v, done,
+                                       sg);
+        };
+        if (L.grp_rmax <= 4) go(k_smooth_g<TC, KK, 4, JL>);
+        else go(k_smooth_g<TC, KK, 8, JL>);
       } else {
         throw Error(AMG_ERR_INVALID_ARG, "internal: grouped kernels need at least 8 columns");
       }
@@ -154,22 +158,26 @@ template <typename TC>
 inline void launch_restrict_g(int K, const Level& L, const Transfer& T, const TPart& tp, const Level& C,
                               bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, const int* done,
                               cudaStream_t st) {
+  Stage sg = T.gsg;
+  sg.err = tp.sg.err;
+  if (sizeof(TC) != 4) sg.enabled = 0;
+  const size_t smem = pipe_bytes(sg, 1, 1);
   dispatch_k(K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     dispatch_jl(tp.jl, [&](auto jc) {
       constexpr int JL = decltype(jc)::value;
       if constexpr (KK >= 8 && VT<TC, KK>::CL * JL <= 32) {
-        auto go = [&](auto ra, auto rm) {
-          constexpr int RA = decltype(ra)::value, RM = decltype(rm)::value;
-          k_restrict_g<TC, KK, RA, RM, JL><<<T.nagg, RG_WARPS * 32, 0, st>>>(
-              T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), L.gstart, T.gagg, L.rowptr,
-              L.col, vals<TC>(L), f, u, fc, smooth_next ? uc : nullptr, smooth_next ? dinvs<TC>(C) : nullptr,
-              done);
+        auto go = [&](auto kern) {
+          ensure_smem(kern, smem);
+          kern<<<T.nagg, RG_WARPS * 32, smem, st>>>(T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T),
+                                                    L.gstart, T.gagg, L.rowptr, L.col, vals<TC>(L), f, u, fc,
+                                                    smooth_next ? uc : nullptr,
+                                                    smooth_next ? dinvs<TC>(C) : nullptr, done, sg);
         };
-        if (L.grp_rmax <= 4 && tp.ra_max <= 4) go(ic<4>{}, ic<4>{});
-        else if (L.grp_rmax <= 4) go(ic<4>{}, ic<8>{});
-        else if (tp.ra_max <= 4) go(ic<8>{}, ic<4>{});
-        else go(ic<8>{}, ic<8>{});
+        if (L.grp_rmax <= 4 && tp.ra_max <= 4) go(k_restrict_g<TC, KK, 4, 4, JL>);
+        else if (L.grp_rmax <= 4) go(k_restrict_g<TC, KK, 4, 8, JL>);
+        else if (tp.ra_max <= 4) go(k_restrict_g<TC, KK, 8, 4, JL>);
+        else go(k_restrict_g<TC, KK, 8, 8, JL>);
       } else {
         throw Error(AMG_ERR_INVALID_ARG, "internal: grouped kernels need at least 8 columns");
       }
@@ -189,7 +197,7 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   void launch_smooth<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,   \
                          TC* v, const int* done, cudaStream_t st) {                                    \
     if (nzl <= 0) { /* grouped coarse level, -nzl lanes per group column split (0: one) */            \
-      launch_smooth_g<TC>(K, nzl < 0 ? -nzl : 1, L, f, u, v, done, st);                               \
+      launch_smooth_g<TC>(K, nzl < 0 ? -nzl : 1, L, f, u, v, done, st, rp.sg.err);                    \
       return;                                                                                          \
     }                                                                                                  \
     size_t smem = csr_stage_bytes<TC>(rp.sg);                                                          \

@@ -1349,6 +1349,21 @@ __global__ void k_check_groups(int ngrp, const int* __restrict__ gstart, const i
   }
 }
 
+// Staging capacities of CTAs over the row ranges [cr[c], cr[c+1]) of a
+// grouped kernel (float values through the one-buffer pipeline); off when a
+// slice would take more than 96 KB of shared memory.
+static Stage make_group_stage(const std::vector<int>& rp, const std::vector<int>& cr) {
+  Stage sg;
+  for (size_t c = 0; c + 1 < cr.size(); ++c) {
+    const int r0 = cr[c], r1 = cr[c + 1], j0 = rp[r0], j1 = rp[r1];
+    sg.rows_max = std::max(sg.rows_max, r1 - r0);
+    sg.span4 = std::max(sg.span4, ((j1 + 3) & ~3) - (j0 & ~3));
+  }
+  sg.enabled = 1;
+  if (pipe_bytes(sg, 1, 1) > 96 * 1024) sg.enabled = 0;
+  return sg;
+}
+
 static void ensure_groups(Plan& P) {
   if (P.groups_done) return;
   P.groups_done = true;
@@ -1382,6 +1397,11 @@ static void ensure_groups(Plan& P) {
     L.ngrp = T.nagg;
     L.grp_rmax = rmax;
     L.gstart = T.coarse_start;
+    // staging capacities of the grouped sweep's CTAs
+    std::vector<int> cr;
+    for (int g = 0; g < T.nagg; g += GROUPS_PER_CTA) cr.push_back(gs[g]);
+    cr.push_back(gs[T.nagg]);
+    L.gsg = make_group_stage(L.h_rowptr, cr);
   }
   for (int k = 1; k + 1 < P.L; ++k) {
     if (!P.lev[k].grp_ok) continue;
@@ -1399,6 +1419,7 @@ static void ensure_groups(Plan& P) {
     int* d = P.arena->alloc<int>(ga.size());
     AMG_CUDA(cudaMemcpy(d, ga.data(), ga.size() * sizeof(int), cudaMemcpyHostToDevice));
     P.tr[k].gagg = d;
+    P.tr[k].gsg = make_group_stage(P.lev[k].h_rowptr, rs);  // one CTA per aggregate
   }
 }
 
