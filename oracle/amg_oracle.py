@@ -262,3 +262,67 @@ def coarsening_ratio(H: Hierarchy) -> float:
     if len(n) < 2:
         return 1.0
     return float(np.mean([n[k - 1] / n[k] for k in range(1, len(n))]))
+
+
+# --------------------------------------------------------------------------
+# bootstrap (Algorithm 1, Section 2): the testing phase and the driver
+# --------------------------------------------------------------------------
+
+def composite_error(Hs, A, x, symmetric: bool = True):
+    """One application of the composite error operator of Algorithm 1 to x
+    (vector or n x K).  With hierarchies H_1..H_r (B_k one V-cycle of H_k)
+    the plain product is E = (I - B_r A) ... (I - B_1 A), Eq. (comp_AMG):
+    the rightmost factor acts first.  The symmetrized product of Section 5
+    (i) is (I - B_1 A) ... (I - B_r A) (I - B_r A) ... (I - B_1 A): factors
+    1, 2, ..., r, then r, ..., 2, 1."""
+    order = list(range(len(Hs)))
+    seq = order + order[::-1] if symmetric else order
+    v = np.array(x, dtype=np.float64)
+    for k in seq:
+        v = v - vcycle(Hs[k], A @ v)
+    return v
+
+
+def a_norm(A, x):
+    """||x||_A per column."""
+    X = np.asarray(x, dtype=np.float64)
+    X2 = X[:, None] if X.ndim == 1 else X
+    return np.sqrt(np.einsum("ij,ij->j", X2, A @ X2))
+
+
+def bootstrap_test(Hs, A, x0, nu: int, symmetric: bool = True):
+    """Testing phase of Algorithm 1: x^j = E x^{j-1}, j = 1..nu, from x^0 =
+    x0.  Returns (x^nu, rho) with the convergence estimate rho =
+    (||x^nu||_A / ||x^0||_A)^(1/nu) per column (the paper leaves the estimate
+    unstated; this is the mean A-norm reduction per application)."""
+    x = np.array(x0, dtype=np.float64)
+    n0 = a_norm(A, x)
+    for _ in range(nu):
+        x = composite_error(Hs, A, x, symmetric)
+    n1 = a_norm(A, x)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rho = np.where(n0 > 0, (n1 / n0) ** (1.0 / nu), 0.0)
+    return x, rho
+
+
+def bootstrap(A, w0, m: int, nu: int, aggregate, starts, symmetric: bool = True, tol: float = 0.1):
+    """Algorithm 1 with maxstage = m - 1 and rho_des = 0 (the number of
+    smooth vectors is fixed instead of the target rate).  Stage r = 1..m-1
+    builds B_r from w_{r-1}: ``aggregate(w)`` gives the composed pairwise
+    aggregates (aggs, n_nodes) of the weighted matching on w (Section 3), and
+    the hierarchy holds the single smooth vector w (m = 1).  The testing
+    phase applies the composite operator of B_1..B_r nu times to the random
+    vector starts[r-1] and takes w_r = x^nu / ||x^nu||_A.  Returns (W, rhos)
+    with W = [w_0, ..., w_{m-1}] (n x m) and the stage estimates rho."""
+    n = A.shape[0]
+    W = np.empty((n, m))
+    W[:, 0] = w0
+    Hs, rhos = [], []
+    for r in range(1, m):
+        w = W[:, r - 1]
+        aggs, n_nodes = aggregate(w)
+        Hs.append(setup(A, aggs, n_nodes, (w / np.linalg.norm(w))[:, None], tol))
+        x, rho = bootstrap_test(Hs, A, starts[r - 1], nu, symmetric)
+        W[:, r] = x / a_norm(A, x)[0]
+        rhos.append(float(rho[0]))
+    return W, rhos

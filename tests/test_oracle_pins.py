@@ -313,3 +313,89 @@ def test_complexity_metrics():
     assert opc == pytest.approx(sum(l.A.nnz for l in H.levels) / A.nnz)
     n = [l.A.shape[0] for l in H.levels]
     assert O.coarsening_ratio(H) == pytest.approx(np.mean([n[0] / n[1], n[1] / n[2]]))
+
+
+# ------------------------------------------------- bootstrap (Algorithm 1) --
+
+def _bootstrap_hierarchies(N=10):
+    """Two single-vector hierarchies on one aniso9 operator, built from two
+    different vectors (so the aggregates differ), as stages B_1, B_2."""
+    A = problems.aniso9(N)
+    n = A.shape[0]
+    w1 = np.ones(n)
+    w2 = np.random.default_rng(21).standard_normal(n)
+    Hs = []
+    for w, steps in ((w1, [2]), (w2, [2, 2])):
+        aggs, nn = aggregation.aggregate_hierarchy(A, w, steps)
+        Hs.append(O.setup(A, aggs, nn, (w / np.linalg.norm(w))[:, None]))
+    return A, Hs
+
+
+def test_bootstrap_composite_matches_dense_product():
+    """Eq. (comp_AMG) applies (I - B_1 A) first; the symmetrized product of
+    Section 5 (i) is (I - B_1 A)(I - B_2 A)(I - B_2 A)(I - B_1 A)."""
+    A, Hs = _bootstrap_hierarchies()
+    n = A.shape[0]
+    Ad = A.toarray()
+    E1 = np.eye(n) - _dense_B(Hs[0], n) @ Ad
+    E2 = np.eye(n) - _dense_B(Hs[1], n) @ Ad
+    x = np.random.default_rng(5).standard_normal((n, 3))
+    np.testing.assert_allclose(O.composite_error(Hs, A, x, symmetric=False), E2 @ E1 @ x, atol=1e-12)
+    np.testing.assert_allclose(O.composite_error(Hs, A, x, symmetric=True), E1 @ E2 @ E2 @ E1 @ x, atol=1e-12)
+    # the order matters: the reversed product differs
+    assert np.abs(E1 @ E2 @ x - E2 @ E1 @ x).max() > 1e-6
+
+
+def test_bootstrap_symmetric_product_is_a_selfadjoint_contraction():
+    """With SPD V-cycles each I - B_k A is A-self-adjoint with A-norm < 1, so
+    the symmetrized product is A-self-adjoint with spectrum in [0, 1)."""
+    A, Hs = _bootstrap_hierarchies()
+    n = A.shape[0]
+    E = np.stack([O.composite_error(Hs, A, e, symmetric=True) for e in np.eye(n)], axis=1)
+    AE = A.toarray() @ E
+    np.testing.assert_allclose(AE, AE.T, atol=1e-12 * np.abs(AE).max())
+    lam = sla.eigh(AE, A.toarray(), eigvals_only=True)
+    assert lam.min() > -1e-12 and lam.max() < 1.0
+
+
+def test_bootstrap_rho_tends_to_the_largest_eigenvalue():
+    """rho = (||x^nu||_A / ||x^0||_A)^(1/nu) is a power iteration on the
+    symmetrized product: for large nu it approaches its largest eigenvalue."""
+    A, Hs = _bootstrap_hierarchies()
+    n = A.shape[0]
+    E = np.stack([O.composite_error(Hs, A, e, symmetric=True) for e in np.eye(n)], axis=1)
+    lam_max = sla.eigh(A.toarray() @ E, A.toarray(), eigvals_only=True).max()
+    x0 = np.random.default_rng(8).standard_normal(n)
+    x100, rho100 = O.bootstrap_test(Hs, A, x0, nu=100, symmetric=True)
+    _, rho = O.bootstrap_test(Hs, A, x100, nu=100, symmetric=True)  # from an already aligned start
+    assert abs(rho[0] - lam_max) <= 5e-3 * lam_max
+    assert rho100[0] <= lam_max * (1 + 1e-12)  # no A-norm reduction factor exceeds the spectral radius
+    _, rho1 = O.bootstrap_test(Hs, A, x0, nu=1, symmetric=True)
+    np.testing.assert_allclose(rho1[0], O.a_norm(A, E @ x0)[0] / O.a_norm(A, x0)[0], rtol=1e-12)
+
+
+def test_bootstrap_one_level_stage_annihilates():
+    """A one-level hierarchy solves exactly (B = A^{-1}): I - B A = 0."""
+    A = problems.poisson5(8)
+    H = O.setup(A, [], [64], np.ones((64, 1)))
+    x0 = np.random.default_rng(2).standard_normal((64, 2))
+    x, rho = O.bootstrap_test([H], A, x0, nu=3)
+    assert np.abs(x).max() <= 1e-12 * np.abs(x0).max()
+    assert np.all(rho <= 1e-10)
+
+
+def test_bootstrap_driver_stages():
+    """Stage r builds B_r from w_{r-1}, tests B_1..B_r on starts[r-1] and
+    stores w_r = x^nu / ||x^nu||_A."""
+    A = problems.poisson5(12)
+    n = A.shape[0]
+    agg = lambda w: aggregation.aggregate_hierarchy(A, w, [2, 2])
+    starts = [np.random.default_rng(30 + r).standard_normal(n) for r in range(2)]
+    W, rhos = O.bootstrap(A, np.ones(n), 3, 5, agg, starts)
+    np.testing.assert_allclose(O.a_norm(A, W[:, 1:]), 1.0, rtol=1e-12)
+    aggs, nn = agg(np.ones(n))
+    H1 = O.setup(A, aggs, nn, np.full((n, 1), 1.0 / np.sqrt(n)))
+    x1, r1 = O.bootstrap_test([H1], A, starts[0], 5)
+    np.testing.assert_allclose(W[:, 1], x1 / O.a_norm(A, x1)[0], atol=1e-12)
+    assert rhos[0] == pytest.approx(r1[0], rel=1e-12)
+    assert 0.0 < rhos[1] < 1.0
