@@ -169,6 +169,27 @@ amg_status amg_adjoint(amg_handle h, const double* g, const double* x, int32_t n
 amg_status amg_vcycle(amg_handle h, const double* r, double* z, int32_t nrhs,
                       const amg_opts* opts, void* stream);
 
+/*
+ * Testing phase of the bootstrap (Algorithm 1, Section 2).  hs[0..r-1] are
+ * hierarchies B_1..B_r, all set up on the same matrix A (same order and
+ * non-zeros; the level-0 copy of hs[0] serves as A).  x (n x nrhs
+ * row-major float64, host or device, the caller's numbering, nrhs <= 32) is
+ * replaced in place by E^nu x, where with B_k one V-cycle of hs[k] in
+ * opts->cycle_precision
+ *     symmetric != 0:  E = (I - B_1 A) ... (I - B_r A) (I - B_r A) ... (I - B_1 A)
+ *                      (the symmetrized product of Section 5 (i)),
+ *     symmetric == 0:  E = (I - B_r A) ... (I - B_1 A)   (Eq. (comp_AMG)).
+ * rho (nrhs doubles, host, may be NULL) receives the convergence estimate
+ * (||E^nu x||_A / ||x||_A)^(1/nu) per column (0 for a zero column), and
+ * anorm (nrhs doubles, host, may be NULL) ||E^nu x||_A, which normalises the
+ * new smooth vector (w_r = x^nu / ||x^nu||_A).  The call allocates its own
+ * work vectors and synchronises ``stream`` before it returns.  Mismatched
+ * hierarchies or sizes give AMG_ERR_INVALID_ARG.
+ */
+amg_status amg_bootstrap_test(const amg_handle* hs, int32_t r, double* x, int32_t nrhs, int32_t nu,
+                              int32_t symmetric, const amg_opts* opts, void* stream, double* rho,
+                              double* anorm);
+
 /* Hierarchy characteristics; never fails for a valid handle. */
 amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info);
 

@@ -89,6 +89,8 @@ SIGNATURES = {
     "amg_kernel_launches": (C.c_int, [C.POINTER(C.c_int64)]),
     "amg_local_bases_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amg_bootstrap_test": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                     C.c_int32, C.POINTER(amg_opts), C.c_void_p, C.c_void_p, C.c_void_p]),
     "amg_destroy": (None, [C.c_void_p]),
     "amg_last_error": (C.c_char_p, []),
 }
@@ -381,3 +383,21 @@ def solve_batched(hs, bs, xs=None, options: amg_opts | None = None, stream=None)
         out.append([_info_dict(infos[o + c]) for c in range(int(nr[s]))])
         o += int(nr[s])
     return x2, out, st
+
+
+def bootstrap_test(hs, x, nu: int, symmetric: bool = True, options: amg_opts | None = None, stream=None):
+    """Testing phase of the bootstrap (amg_bootstrap_test in include/amg.h):
+    returns (E^nu x, rho, ||E^nu x||_A) for the composite error operator of
+    the hierarchies ``hs``.  x: (n,) or (n, k) float64, numpy or torch; the
+    input is not modified (a copy is passed)."""
+    keep = []
+    x2, shape = _as2d(x)
+    x2 = x2.clone() if _is_torch(x2) else x2.copy()
+    k = int(x2.shape[1])
+    rho = np.zeros(k, dtype=np.float64)
+    anorm = np.zeros(k, dtype=np.float64)
+    hp = (C.c_void_p * len(hs))(*[h.h for h in hs])
+    _check(lib().amg_bootstrap_test(hp, len(hs), _ptr(x2, np.float64, keep), k, int(nu), 1 if symmetric else 0,
+                                    C.byref(options) if options is not None else None, _stream(stream),
+                                    rho.ctypes.data, anorm.ctypes.data))
+    return _reshape(x2, shape), rho, anorm

@@ -214,6 +214,22 @@ amg_status amg_vcycle(amg_handle h, const double* r, double* z, int32_t nrhs, co
   });
 }
 
+amg_status amg_bootstrap_test(const amg_handle* hs, int32_t r, double* x, int32_t nrhs, int32_t nu,
+                              int32_t symmetric, const amg_opts* opts, void* stream, double* rho,
+                              double* anorm) {
+  if (!hs || !x || r < 1) return fail(AMG_ERR_INVALID_ARG, "null argument or r < 1");
+  if (nrhs < 1 || nrhs > 32) return fail(AMG_ERR_INVALID_ARG, "nrhs must be in [1, 32]");
+  if (nu < 1) return fail(AMG_ERR_INVALID_ARG, "nu must be >= 1");
+  for (int k = 0; k < r; ++k)
+    if (!hs[k]) return fail(AMG_ERR_INVALID_ARG, "null hierarchy");
+  return guarded([&]() -> amg_status {
+    amg_opts o = resolve(opts);
+    std::vector<amg_hierarchy*> v(hs, hs + r);
+    amg::run_bootstrap_test(v, x, nrhs, nu, symmetric, o, as_stream(stream), rho, anorm);
+    return AMG_OK;
+  });
+}
+
 amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info) {
   if (!h || !info) return fail(AMG_ERR_INVALID_ARG, "null argument");
   std::memset(info, 0, sizeof(*info));

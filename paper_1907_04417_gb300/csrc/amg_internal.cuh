@@ -131,6 +131,7 @@ struct TPart {
   int warp = 0;    // restriction: 0 CTA ranges, 1 one warp per aggregate, 2 grouped (one CTA per aggregate)
   int pwarp = 0;   // prolongation by one warp per aggregate (no CTA ranges)
   int jl = 1;      // grouped restriction: lanes splitting a group's pattern columns
+  Stage wsg;       // staging of the warp-per-aggregate restriction (NWARP aggregates per CTA)
 };
 
 // Row ranges of the row-parallel kernels of one level for a given column
@@ -218,6 +219,10 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
                 const amg_opts& o, cudaStream_t user);
 void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* x_caller,
                       int nrhs, double* grad, cudaStream_t st);
+
+// bootstrap testing phase (amg_bootstrap.cu)
+void run_bootstrap_test(const std::vector<amg_hierarchy*>& hs, double* x, int nrhs, int nu, int symmetric,
+                        const amg_opts& o, cudaStream_t st, double* rho, double* anorm);
 
 // launch accounting
 extern thread_local bool g_capturing;

@@ -45,3 +45,13 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.amg_hierarchy_info(None, None) == amg.AMG_ERR_INVALID_ARG
     out = ctypes.c_void_p()
     assert lib.amg_setup_from_aggregates(None, 0, None, None, None, 1, None, None, ctypes.byref(out)) != amg.AMG_OK
+
+
+def test_bootstrap_test_rejects_bad_arguments_without_gpu(lib):
+    import ctypes
+    hp = (ctypes.c_void_p * 1)(None)
+    assert lib.amg_bootstrap_test(None, 1, None, 1, 1, 1, None, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert lib.amg_bootstrap_test(hp, 0, None, 1, 1, 1, None, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    x = (ctypes.c_double * 4)()
+    assert lib.amg_bootstrap_test(hp, 1, x, 1, 1, 1, None, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "hierarchy" in amg.last_error()
