@@ -215,6 +215,22 @@ def algorithmic_bytes(kernel, lv, K, wc):
 
 KERNEL_IDS = {"spmv_cg": 1, "restrict_l0": 2, "smooth_l0": 3, "prolong_l0": 4, "cg_update": 5}
 
+# q = A p in double-float is bound by float32 arithmetic: per stored non-zero
+# and column the multiply-accumulate of a float pair by a float32 takes 11
+# float32 operations (exact product 2, low-part product 1, two-sum 6, error
+# accumulation 2); per row and column the renormalisation (3) and the
+# double-float p.q step (11) follow.  Peak: 152 SMs x 128 float32 lanes x
+# 2.07 GHz (the maximum SM clock) = 40.3e12 lane operations per second.
+ALU_OPS_PER_NZ_COL = 11
+ALU_OPS_PER_ROW_COL = 14
+ALU_PEAK_OPS = 152 * 128 * 2.07e9
+
+
+def alu_ops(kernel, lv, K):
+    if kernel == "spmv_cg":
+        return lv["nnz0"] * K * ALU_OPS_PER_NZ_COL + lv["n0"] * K * ALU_OPS_PER_ROW_COL
+    return None
+
 
 # ------------------------------------------------------------ CPU legs --
 def oracle_sample(P, iters_needed, budget_s):
@@ -411,6 +427,16 @@ def main():
             "traffic": stored_traffic(rk, f"aniso{args.grid}_K{args.batch}"), "kernel": rk,
             "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": abytes,
             "avg_launch_ms": avg_ms, "launches_timed": kn}
+    ops = alu_ops(rk, lv, args.batch)
+    if ops is not None and avg_ms > 0:
+        # the double-float q = A p: float32 arithmetic bounds it (DRAM runs at
+        # under half of the copy peak); its HBM figures stay beside it
+        aa = ops / (avg_ms * 1e-3) / 1e12
+        roof.update({"bound": "alu", "achieved": aa, "peak": ALU_PEAK_OPS / 1e12,
+                     "unit": "T float32 ops/s", "frac": aa * 1e12 / ALU_PEAK_OPS,
+                     "peak_source": "derived: 152 SMs x 128 float32 lanes x 2.07 GHz",
+                     "alu_ops_per_launch": ops, "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
+                     "hbm_frac": achieved / peak})
 
     line = {"metric": METRIC, "value": value_job, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": False, "scaling": "weak",

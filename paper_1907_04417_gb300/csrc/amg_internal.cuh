@@ -128,7 +128,7 @@ struct TPart {
   int rows_max = 0, p_max = 0, a_max = 0, c_max = 0;
   int ra_max = 1;  // largest number of coarse dofs of one aggregate
   Stage sg;
-  int warp = 0;    // restriction: 0 CTA ranges, 1 one warp per aggregate, 2 grouped (one CTA per aggregate)
+  int warp = 0;    // restriction: 0 CTA ranges, 1 one warp per aggregate (3: staged), 2 grouped (one CTA per aggregate)
   int pwarp = 0;   // prolongation by one warp per aggregate (no CTA ranges)
   int jl = 1;      // grouped restriction: lanes splitting a group's pattern columns
   Stage wsg;       // staging of the warp-per-aggregate restriction (NWARP aggregates per CTA)

@@ -189,6 +189,32 @@ struct CsrView {
   int voff;
 };
 
+// A CTA whose rows form one contiguous range [r0, r1) covers one contiguous
+// non-zero range; with float values it can stage that slice (rowptr, col,
+// values) into shared memory with bulk TMA copies first (one buffer of the
+// pipeline below), so that its gathers wait on nothing but themselves.
+template <typename TC>
+__device__ __forceinline__ CsrView<TC> group_view(const Stage& sg, unsigned char* smem, int r0, int r1,
+                                                  const int* __restrict__ rowptr, const int* __restrict__ col,
+                                                  const TC* __restrict__ val) {
+  if constexpr (sizeof(TC) == 4) {
+    if (sg.enabled) {
+      pipe_init(smem);
+      if (threadIdx.x == 0) {
+        const float* v1[1] = {reinterpret_cast<const float*>(val)};
+        pipe_issue<1>(sg, smem, 0, r0, r1, rowptr, col, v1);
+      }
+      const int* rp;
+      const int* cs;
+      const float* vs[1];
+      int roff, joff;
+      pipe_wait<1>(sg, smem, 0, 0, r0, rowptr, rp, roff, cs, vs, joff);
+      return CsrView<TC>{rp, roff, cs, joff, reinterpret_cast<const TC*>(vs[0]), joff};
+    }
+  }
+  return CsrView<TC>{rowptr, 0, col, 0, val, 0};
+}
+
 // Stage rows [r0, r1): col plus NV value arrays of widths vw[] (4 or 8).
 template <int NV>
 __device__ __forceinline__ bool stage_csr(const Stage& sg, unsigned char* smem, int r0, int r1,
@@ -736,17 +762,21 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
                                                    const int* __restrict__ col, const TC* __restrict__ val,
                                                    const TC* __restrict__ f, const TC* __restrict__ u,
                                                    TC* __restrict__ fc, TC* __restrict__ uc,
-                                                   const TC* __restrict__ dinvc, const int* __restrict__ done) {
+                                                   const TC* __restrict__ dinvc, const int* __restrict__ done,
+                                                   Stage sg) {
   if (*done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
   const int lane = threadIdx.x & 31;
   const int g = lane / CL, cl = lane % CL;
-  const int a = blockIdx.x * NWARP + (threadIdx.x >> 5);
+  // the CTA's NWARP aggregates are one row range (staged when sg is enabled)
+  const int a0 = blockIdx.x * NWARP, a1 = min(a0 + NWARP, nagg);
+  const CsrView<TC> cv = group_view<TC>(sg, smraw, __ldg(row_start + a0), __ldg(row_start + a1), rowptr, col, val);
+  const int a = a0 + (threadIdx.x >> 5);
   if (a >= nagg) return;  // whole warp
   const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
   const int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
   const TC* Pa = P + __ldg(blk_start + a);
-  const CsrView<TC> cv{rowptr, 0, col, 0, val, 0};
   TC acc[RMAX][CPT];
 #pragma unroll
   for (int p = 0; p < RMAX; ++p)
@@ -807,32 +837,6 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
 // shuffles; there are 32 / (CL JL) slots per warp.
 constexpr int GATHER_G = 10;   // gathers in flight per lane in the grouped kernels
 constexpr int GROUPS_PER_CTA = 32;  // row groups of one grouped-sweep CTA
-
-// A CTA's row groups cover one contiguous row range and hence one
-// contiguous non-zero range; with float values the CTA stages that slice
-// (rowptr, col, values) into shared memory with bulk TMA copies first, so the
-// gathers of u wait on nothing but themselves.
-template <typename TC>
-__device__ __forceinline__ CsrView<TC> group_view(const Stage& sg, unsigned char* smem, int r0, int r1,
-                                                  const int* __restrict__ rowptr, const int* __restrict__ col,
-                                                  const TC* __restrict__ val) {
-  if constexpr (sizeof(TC) == 4) {
-    if (sg.enabled) {
-      pipe_init(smem);
-      if (threadIdx.x == 0) {
-        const float* v1[1] = {reinterpret_cast<const float*>(val)};
-        pipe_issue<1>(sg, smem, 0, r0, r1, rowptr, col, v1);
-      }
-      const int* rp;
-      const int* cs;
-      const float* vs[1];
-      int roff, joff;
-      pipe_wait<1>(sg, smem, 0, 0, r0, rowptr, rp, roff, cs, vs, joff);
-      return CsrView<TC>{rp, roff, cs, joff, reinterpret_cast<const TC*>(vs[0]), joff};
-    }
-  }
-  return CsrView<TC>{rowptr, 0, col, 0, val, 0};
-}
 
 template <typename TC, int K, int RA, int JL>
 __device__ __forceinline__ void group_acc(int r0, int ra, const CsrView<TC>& cv, const TC* __restrict__ x, int cl,
@@ -1054,10 +1058,10 @@ __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg,
 }
 
 // u[rows(a)] += P_a uc[coarse(a)] with one warp per aggregate: CL lanes
-// per row (CPT columns each), 32 / CL rows per pass; the prolongator row and
-// the aggregate's coarse values are read straight from global memory (the
-// coarse rows are shared by the aggregate's rows through L1).
-template <typename TC, int K>
+// per row (CPT columns each), 32 / CL rows per pass.  Each lane reads its
+// columns of the aggregate's RMAX (>= r_a) coarse values once and keeps them
+// in registers; two rows are loaded before either is updated.
+template <typename TC, int K, int RMAX>
 __global__ void __launch_bounds__(BS) k_prolong_w(int nagg, const int* __restrict__ row_start,
                                                   const int* __restrict__ coarse_start,
                                                   const long long* __restrict__ blk_start,
@@ -1071,24 +1075,43 @@ __global__ void __launch_bounds__(BS) k_prolong_w(int nagg, const int* __restric
   const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
   const int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
   const TC* Pa = P + __ldg(blk_start + a);
-  const TC* ucp = uc + (size_t)cs * K + cl * CPT;
-  for (int i = rs + lane / CL; i < re; i += RPW) {
-    const TC* pr = Pa + (size_t)(i - rs) * ra;
-    TC* up = u + (size_t)i * K + cl * CPT;
-    TC sv[CPT], uv[CPT];
+  TC cv[RMAX][CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) sv[t] = TC(0);
-    for (int p = 0; p < ra; ++p) {  // the same order as k_prolong: P_a row . uc, then added to u
-      const TC pv = __ldg(pr + p);
-      TC cv[CPT];
-      ldv<TC, CPT>(ucp + (size_t)p * K, cv);
+  for (int p = 0; p < RMAX; ++p) {
+    if (p < ra) {
+      ldv<TC, CPT>(uc + (size_t)(cs + p) * K + cl * CPT, cv[p]);
+    } else {
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) sv[t] = fma(pv, cv[t], sv[t]);
+      for (int t = 0; t < CPT; ++t) cv[p][t] = TC(0);
     }
-    ldp<TC, CPT>(up, uv);
+  }
+  for (int i = rs + lane / CL; i < re; i += 2 * RPW) {
+    const int i2 = i + RPW;
+    const bool two = i2 < re;
+    TC pv[2][RMAX], uv[2][CPT];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) uv[t] += sv[t];
-    stv<TC, CPT>(up, uv);
+    for (int p = 0; p < RMAX; ++p) {
+      pv[0][p] = p < ra ? __ldg(Pa + (size_t)(i - rs) * ra + p) : TC(0);
+      pv[1][p] = (two && p < ra) ? __ldg(Pa + (size_t)(i2 - rs) * ra + p) : TC(0);
+    }
+    ldp<TC, CPT>(u + (size_t)i * K + cl * CPT, uv[0]);
+    if (two) ldp<TC, CPT>(u + (size_t)i2 * K + cl * CPT, uv[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      // the same order as k_prolong: P_a row . uc, then added to u
+      TC sv[CPT];
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) sv[t] = TC(0);
+#pragma unroll
+      for (int p = 0; p < RMAX; ++p)
+        if (p < ra)
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) sv[t] = fma(pv[h][p], cv[p][t], sv[t]);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) uv[h][t] += sv[t];
+    }
+    stv<TC, CPT>(u + (size_t)i * K + cl * CPT, uv[0]);
+    if (two) stv<TC, CPT>(u + (size_t)i2 * K + cl * CPT, uv[1]);
   }
 }
 

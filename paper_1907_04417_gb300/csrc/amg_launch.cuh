@@ -231,10 +231,16 @@ inline size_t csr_stage_bytes(const Stage& sg) {
         constexpr int KK = decltype(kc)::value;                                                        \
         auto go = [&](auto rc) {                                                                       \
           constexpr int RM = decltype(rc)::value;                                                      \
-          k_restrict_w<TC, KK, RM><<<(T.nagg + NWARP - 1) / NWARP, BS, 0, st>>>(                       \
+          Stage wsg = tp.wsg; /* kind 3 stages the CTA's slice, kind 1 reads global memory */          \
+          wsg.err = tp.sg.err;                                                                         \
+          if (sizeof(TC) != 4 || tp.warp != 3) wsg.enabled = 0;                                        \
+          const size_t wsm = pipe_bytes(wsg, 1, 1);                                                    \
+          auto kern = k_restrict_w<TC, KK, RM>;                                                        \
+          ensure_smem(kern, wsm);                                                                      \
+          kern<<<(T.nagg + NWARP - 1) / NWARP, BS, wsm, st>>>(                                         \
               T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), L.rowptr, L.col,         \
               vals<TC>(L), f, u, fc, smooth_next ? uc : nullptr, smooth_next ? dinvs<TC>(C) : nullptr, \
-              done);                                                                                   \
+              done, wsg);                                                                              \
         };                                                                                             \
         if (tp.ra_max <= 4) go(std::integral_constant<int, 4>{});                                      \
         else if (tp.ra_max <= 8) go(std::integral_constant<int, 8>{});                                 \
@@ -267,11 +273,16 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   template <>                                                                                          \
   void launch_prolong<TC>(int K, const Transfer& T, const TPart& tp, const TC* uc, TC* u,             \
                           const int* done, cudaStream_t st) {                                          \
-    if (tp.pwarp) {                                                                                    \
+    if (tp.pwarp && tp.ra_max <= 8) {                                                                  \
       dispatch_k(K, [&](auto kc) {                                                                     \
         constexpr int KK = decltype(kc)::value;                                                        \
-        k_prolong_w<TC, KK><<<(T.nagg + NWARP - 1) / NWARP, BS, 0, st>>>(                              \
-            T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), uc, u, done);              \
+        const int grid = (T.nagg + NWARP - 1) / NWARP;                                                 \
+        if (tp.ra_max <= 4)                                                                            \
+          k_prolong_w<TC, KK, 4><<<grid, BS, 0, st>>>(T.nagg, T.row_start, T.coarse_start, T.blk_start, \
+                                                      pvals<TC>(T), uc, u, done);                      \
+        else                                                                                           \
+          k_prolong_w<TC, KK, 8><<<grid, BS, 0, st>>>(T.nagg, T.row_start, T.coarse_start, T.blk_start, \
+                                                      pvals<TC>(T), uc, u, done);                      \
       });                                                                                              \
       AMG_LAUNCH_CHECK();                                                                              \
       return;                                                                                          \

@@ -726,6 +726,21 @@ static RPart make_flat(Arena& ar, int ncta) {
   return p;
 }
 
+// Staging capacities of CTAs over the row ranges [cr[c], cr[c+1]) of a
+// grouped kernel (float values through the one-buffer pipeline); off when a
+// slice would take more than 96 KB of shared memory.
+static Stage make_group_stage(const std::vector<int>& rp, const std::vector<int>& cr) {
+  Stage sg;
+  for (size_t c = 0; c + 1 < cr.size(); ++c) {
+    const int r0 = cr[c], r1 = cr[c + 1], j0 = rp[r0], j1 = rp[r1];
+    sg.rows_max = std::max(sg.rows_max, r1 - r0);
+    sg.span4 = std::max(sg.span4, ((j1 + 3) & ~3) - (j0 & ~3));
+  }
+  sg.enabled = 1;
+  if (pipe_bytes(sg, 1, 1) > 96 * 1024) sg.enabled = 0;
+  return sg;
+}
+
 static TPart make_tpart(Arena& ar, const Transfer& T, const Level& F, int K, int* err, int target = 0) {
   if (target <= 0) target = K <= 2 ? 256 : (K <= 8 ? 128 : 64);
   std::vector<int> ca{0};
@@ -754,6 +769,12 @@ static TPart make_tpart(Arena& ar, const Transfer& T, const Level& F, int K, int
   std::vector<int> cr(ca.size());
   for (size_t c = 0; c < ca.size(); ++c) cr[c] = T.h_row_start[ca[c]];
   tp.sg = make_stage(F.h_rowptr, cr, err);
+  // the warp-per-aggregate restriction: NWARP aggregates per CTA
+  std::vector<int> wr;
+  for (int a = 0; a < T.nagg; a += NWARP) wr.push_back(T.h_row_start[a]);
+  wr.push_back(T.h_row_start[T.nagg]);
+  tp.wsg = make_group_stage(F.h_rowptr, wr);
+  tp.wsg.enabled = tp.wsg.enabled && tp.sg.enabled;  // a level read unstaged stays unstaged
   return tp;
 }
 
@@ -1025,27 +1046,36 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     }
     AMG_CUDA(cudaDeviceSynchronize());
   }
-  // the warp-per-aggregate restriction (no CTA ranges, no staging)
-  bool warp_best = false;
+  // the warp-per-aggregate restriction (no CTA ranges): kind 1 reads the
+  // matrix straight from global memory, kind 3 stages each CTA's slice first
+  int warp_kind = 0;
   if (W.tp[k].ra_max <= 8) {
-    TPart tw = W.tp[k];
-    tw.warp = 1;
-    auto run = [&] {
-      launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], tw, P.lev[k + 1], k + 1 < P.L - 1,
-                          static_cast<TC*>(W.f[k]), static_cast<TC*>(W.u[k]), static_cast<TC*>(W.f[k + 1]),
-                          static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
-    };
-    run();
-    AMG_CUDA(cudaEventRecord(e0, 0));
-    for (int r = 0; r < 3; ++r) run();
-    AMG_CUDA(cudaEventRecord(e1, 0));
-    AMG_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (tune_log()) fprintf(stderr, "[tune] level %d K %d restrict warp-per-aggregate: %.1f us\n", k, K, ms * 1e3 / 3);
-    warp_best = ms < best;
-    if (warp_best) best = ms;
+    for (int kind : {1, 3}) {
+      TPart tw = W.tp[k];
+      tw.warp = kind;
+      if (kind == 3 && !tw.wsg.enabled) continue;
+      auto run = [&] {
+        launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], tw, P.lev[k + 1], k + 1 < P.L - 1,
+                            static_cast<TC*>(W.f[k]), static_cast<TC*>(W.u[k]), static_cast<TC*>(W.f[k + 1]),
+                            static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
+      };
+      run();
+      AMG_CUDA(cudaEventRecord(e0, 0));
+      for (int r = 0; r < 3; ++r) run();
+      AMG_CUDA(cudaEventRecord(e1, 0));
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (tune_log())
+        fprintf(stderr, "[tune] level %d K %d restrict warp-per-aggregate%s: %.1f us\n", k, K,
+                kind == 3 ? " staged" : "", ms * 1e3 / 3);
+      if (ms < best) {
+        best = ms;
+        warp_kind = kind;
+      }
+    }
   }
+  const bool warp_best = warp_kind != 0;
   // the grouped restriction (one CTA per aggregate) out of a grouped level
   bool grp_best = false;
   int gjl = 1;
@@ -1084,6 +1114,7 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     TPart tp = bt > 0 ? make_tpart(tmp, P.tr[k], P.lev[k], K, W.err, bt) : W.tp[k];
     float pbest = 1e30f;
     for (int w : {0, 1}) {
+      if (w == 1 && tp.ra_max > 8) continue;  // the warp prolongation keeps at most 8 coarse values
       tp.pwarp = w;
       auto run = [&] {
         launch_prolong<TC>(K, P.tr[k], tp, static_cast<TC*>(W.v[k + 1]), static_cast<TC*>(W.u[k]), W.zero_flag, 0);
@@ -1106,7 +1137,7 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const int jsel = gjl == 4 ? 2 : (gjl == 2 ? 1 : 0);
-  apply_transfer(P, W, k, bt, bs, (grp_best ? 2 : (warp_best ? 1 : 0)) + 4 * pw + 8 * jsel);
+  apply_transfer(P, W, k, bt, bs, (grp_best ? 2 : (warp_best ? warp_kind : 0)) + 4 * pw + 8 * jsel);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
@@ -1347,21 +1378,6 @@ __global__ void k_check_groups(int ngrp, const int* __restrict__ gstart, const i
     for (int j = lane; j < S; j += 32)
       if (col[br + j] != col[b0 + j]) atomicOr(bad, 1);
   }
-}
-
-// Staging capacities of CTAs over the row ranges [cr[c], cr[c+1]) of a
-// grouped kernel (float values through the one-buffer pipeline); off when a
-// slice would take more than 96 KB of shared memory.
-static Stage make_group_stage(const std::vector<int>& rp, const std::vector<int>& cr) {
-  Stage sg;
-  for (size_t c = 0; c + 1 < cr.size(); ++c) {
-    const int r0 = cr[c], r1 = cr[c + 1], j0 = rp[r0], j1 = rp[r1];
-    sg.rows_max = std::max(sg.rows_max, r1 - r0);
-    sg.span4 = std::max(sg.span4, ((j1 + 3) & ~3) - (j0 & ~3));
-  }
-  sg.enabled = 1;
-  if (pipe_bytes(sg, 1, 1) > 96 * 1024) sg.enabled = 0;
-  return sg;
 }
 
 static void ensure_groups(Plan& P) {
