@@ -42,8 +42,13 @@ def l2_note(nnz, n, batch):
     return f"vector blocks smaller than L2 ({sizes}); not flushed between steps"
 
 
-def workload(N):
-    return f"aniso9 eps=1e-3 theta=pi/6, {N}x{N} (n={N * N}), m=4, aggregates of 16, 5 levels"
+NU_BOOT = 15  # testing-phase applications per bootstrap stage (Algorithm 1)
+
+
+def workload(N, smooth="bootstrap"):
+    sv = ("smooth vectors from the seeded bootstrap (Algorithm 1, nu=15, symmetrized)" if smooth == "bootstrap"
+          else "relaxed random smooth vectors")
+    return f"aniso9 eps=1e-3 theta=pi/6, {N}x{N} (n={N * N}), m=4, aggregates of 16, 5 levels, {sv}"
 PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -55,6 +60,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--smooth", default="bootstrap", choices=["bootstrap", "relaxed"],
+                    help="smooth vectors: the seeded bootstrap of Algorithm 1 (testing phase on the "
+                         "device; the oracle arm runs its own), or the relaxed random vectors")
     ap.add_argument("--maxit", type=int, default=5000)
     ap.add_argument("--roofline-kernel", default="auto")
     ap.add_argument("--tune-cache", default=None,
@@ -233,11 +241,13 @@ def alu_ops(kernel, lv, K):
 
 
 # ------------------------------------------------------------ CPU legs --
-def oracle_sample(P, iters_needed, budget_s):
+def oracle_sample(P, W, iters_needed, budget_s):
     """Time the oracle's PCG iterations on the same workload (setup not
-    timed) for about ``budget_s`` seconds; scale to ``iters_needed``."""
+    timed) for about ``budget_s`` seconds; scale to ``iters_needed``.  W are
+    smooth vectors from the input recipe: the cost of an iteration depends on
+    the hierarchy's sizes, not on the vectors' values."""
     from oracle import amg_oracle as O
-    H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
+    H = O.setup(P.A, P.aggs, P.n_nodes, W)
     b = P.B[:, 0]
     t0 = time.perf_counter()
     r1 = O.pcg(P.A, b, lambda r: O.vcycle(H, r), fixed_iters=1)
@@ -251,10 +261,10 @@ def oracle_sample(P, iters_needed, budget_s):
             "ms_per_rhs": per_it * iters_needed * 1e3, "_first": r1.iters}
 
 
-def stored_oracle_iters(N):
+def stored_oracle_iters(N, smooth="relaxed"):
     p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
     if os.path.exists(p):
-        d = json.load(open(p)).get(f"aniso9_{N}x{N}")
+        d = json.load(open(p)).get(f"aniso9_{N}x{N}" + ("_bootstrap" if smooth == "bootstrap" else ""))
         if d:
             return int(d["iters"])
     return None
@@ -265,8 +275,11 @@ def run_reference(args, ws, rank):
         return
     from paper_1907_04417_gb300.hostsetup import inputs
     P = inputs.anisotropic(N=args.grid, nrhs=1)
-    iters = stored_oracle_iters(args.grid)
+    iters = stored_oracle_iters(args.grid, args.smooth)
     from oracle import amg_oracle as O
+    if args.smooth == "bootstrap":  # the oracle's own bootstrap on the seeded starts (untimed)
+        from oracle.count_iterations import bootstrap_vectors
+        P.W, _ = bootstrap_vectors(P, args.grid)
     H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
     b = P.B[:, 0]
     k = 3
@@ -285,7 +298,7 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_it * k * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload(args.grid), "rhs_per_step": 1},
+            "data": "synthetic", "config": {"workload": workload(args.grid, args.smooth), "rhs_per_step": 1},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{k} FP64 oracle PCG iterations per step on the same workload "
                                        f"(setup untimed), scaled to the oracle's {iters} iterations"},
@@ -315,6 +328,19 @@ def main():
     P = inputs.anisotropic(N=args.grid, nrhs=1)
     B = rhs_block(P, args.batch, rank)
     t_gen = time.time() - t_gen
+    W_recipe = P.W
+    boot = None
+    if args.smooth == "bootstrap":
+        # Algorithm 1 with the testing phase on the device (setup, untimed)
+        from paper_1907_04417_gb300 import bootstrap as boot_mod
+        t_b = time.time()
+        Wb, rhos, Hs = boot_mod.bootstrap(P.A, np.ones(P.n), P.m, NU_BOOT,
+                                          inputs.stage_aggregator(P.A, [4] * (P.levels - 1)),
+                                          inputs.bootstrap_starts(P.n, P.m))
+        for h in Hs:
+            h.close()
+        P.W = Wb / np.linalg.norm(Wb, axis=0)
+        boot = {"nu": NU_BOOT, "rho": rhos, "setup_s": time.time() - t_b}
 
     A = P.A
     Hd = amg.Hierarchy((torch.from_numpy(A.indptr).to(dev), torch.from_numpy(A.indices).to(dev),
@@ -441,7 +467,7 @@ def main():
     line = {"metric": METRIC, "value": value_job, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32-cycle/f64-cg", "data": "synthetic",
-            "config": {"workload": workload(args.grid), "rhs_per_step_per_gpu": args.batch, "rtol": 1e-8,
+            "config": {"workload": workload(args.grid, args.smooth), "rhs_per_step_per_gpu": args.batch, "rtol": 1e-8,
                        "l2": l2_note(P.A.nnz, P.n, args.batch),
                        "parallelism": f"replicas x{ws}"},
             "clocks": cs.summary(), "gpu_launches": launches,
@@ -455,15 +481,15 @@ def main():
             "speedup_batched_vs_fp64_plain": fp64_ms / value_job if value_job else None,
             "hierarchy": {"levels": info_h["levels"], "n": info_h["n_level"], "nnz": info_h["nnz_level"],
                           "opc": info_h["opc"]},
-            "input_gen_s": t_gen}
+            "input_gen_s": t_gen, "bootstrap": boot}
     if shares is not None:
         line["kernel_ms_per_solve"] = shares
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        s = oracle_sample(P, inf64[0]["iters"], args.cpu_sample_s)
+        s = oracle_sample(P, W_recipe, inf64[0]["iters"], args.cpu_sample_s)
         line["cpu_baseline"] = {"value": s["ms_per_rhs"], "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{s['sample_iters']} FP64 oracle PCG iterations on the same "
-                                          f"workload (setup untimed, {s['sample_s']:.1f} s), scaled to "
-                                          f"{inf64[0]['iters']} iterations"}
+                                          f"operator and hierarchy sizes (setup untimed, {s['sample_s']:.1f} s), "
+                                          f"scaled to the {inf64[0]['iters']} iterations of the float64 solve"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     Hd.close()

@@ -5,7 +5,10 @@ generators) and writes tests/golden/oracle_iterations.json.  The benchmark's
 CPU legs time a bounded number of oracle iterations and scale the per-
 iteration time by these counts.
 
-    python oracle/count_iterations.py [grid ...]
+    python oracle/count_iterations.py [--bootstrap] [grid ...]
+
+With --bootstrap the smooth vectors come from the oracle's own bootstrap
+(Algorithm 1) on the seeded starts instead of the relaxed-vector recipe.
 """
 import json
 import os
@@ -23,10 +26,28 @@ from paper_1907_04417_gb300.hostsetup import inputs  # noqa: E402
 OUT = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
 
 
-def main(grids):
+NU = 15  # testing-phase applications per bootstrap stage
+
+
+def bootstrap_vectors(P, N):
+    """The workload's smooth vectors from the oracle's own bootstrap
+    (Algorithm 1): w_0 = 1, m - 1 stages on seeded starts, each vector then
+    scaled to unit 2-norm."""
+    agg = inputs.stage_aggregator(P.A, [4] * (P.levels - 1))
+    W, rhos = O.bootstrap(P.A, np.ones(P.n), P.m, NU, agg, inputs.bootstrap_starts(P.n, P.m))
+    return W / np.linalg.norm(W, axis=0), rhos
+
+
+def main(grids, bootstrap=False):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for N in grids:
         P = inputs.anisotropic(N=N, nrhs=1)
+        key = f"aniso9_{N}x{N}" + ("_bootstrap" if bootstrap else "")
+        note = "FP64 oracle, zero initial guess, RHS seed 1002 uniform[-1,1]"
+        if bootstrap:
+            t0 = time.time()
+            P.W, rhos = bootstrap_vectors(P, N)
+            note += f"; smooth vectors from the oracle's bootstrap (nu {NU}, rho {rhos}, {time.time() - t0:.0f} s)"
         t0 = time.time()
         H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
         ts = time.time() - t0
@@ -34,16 +55,17 @@ def main(grids):
         x, res = O.solve(H, P.B[:, 0], maxit=5000)
         tsol = time.time() - t0
         b = P.B[:, 0]
-        data[f"aniso9_{N}x{N}"] = {
+        data[key] = {
             "iters": res[0].iters, "converged": bool(res[0].converged), "relres": res[0].relres,
             "true_relres": float(np.linalg.norm(b - P.A @ x) / np.linalg.norm(b)),
             "levels": [l.A.shape[0] for l in H.levels], "opc": O.operator_complexity(H),
             "setup_s": ts, "solve_s": tsol, "rtol": 1e-8,
-            "note": "FP64 oracle, zero initial guess, RHS seed 1002 uniform[-1,1]",
+            "note": note,
         }
         json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
-        print(N, data[f"aniso9_{N}x{N}"], flush=True)
+        print(key, data[key], flush=True)
 
 
 if __name__ == "__main__":
-    main([int(a) for a in sys.argv[1:]] or [1024])
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    main([int(a) for a in args] or [1024], bootstrap="--bootstrap" in sys.argv)

@@ -143,3 +143,16 @@ def diffusion_cc(N=512, nrhs=8, m=3, cfg=5, max_coarse=1024):
     Xt = np.repeat(target[:, None], nrhs, axis=1)
     return AMGProblem(f"cc5_{N}x{N}", A, aggs, n_nodes, W, B,
                       {"grid": N, "kcell": k, "x_target": Xt})
+
+
+def bootstrap_starts(n, m, cfg=2):
+    """Seeded start vectors of the bootstrap's testing phase (Algorithm 1):
+    one standard-normal vector per stage r = 1..m-1 (numpy PCG64 seed
+    5000 + 10 cfg + r).  The random numbers the method draws, as input."""
+    return [_rng(5000 + 10 * cfg + r).standard_normal(n) for r in range(1, m)]
+
+
+def stage_aggregator(A, steps):
+    """Aggregates of a bootstrap stage: the composed pairwise steps of the
+    compatible weighted matching on the stage's vector (Section 3)."""
+    return lambda w: aggregation.aggregate_hierarchy(A, w, list(steps))

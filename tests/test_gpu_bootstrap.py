@@ -104,3 +104,27 @@ def test_bootstrap_test_rejects_mismatched_hierarchies(amg):
         amg.bootstrap_test([H1], np.ones(A1.shape[0]), 0)
     H1.close()
     H2.close()
+
+
+def test_bootstrap_workload_iterations_match_oracle(amg):
+    """The benchmark's smooth vectors at 256^2: the device bootstrap on the
+    seeded starts, then the float64 PCG, against the iteration count of the
+    oracle's own bootstrap and solve (stored in tests/golden)."""
+    import json
+    import os
+    from paper_1907_04417_gb300 import bootstrap as B
+    from paper_1907_04417_gb300.hostsetup import inputs
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_iterations.json")))
+    P = inputs.anisotropic(256, nrhs=1)
+    W, rhos, Hs = B.bootstrap(P.A, np.ones(P.n), P.m, 15, inputs.stage_aggregator(P.A, [4] * (P.levels - 1)),
+                              inputs.bootstrap_starts(P.n, P.m))
+    for h in Hs:
+        h.close()
+    H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, W / np.linalg.norm(W, axis=0))
+    x, info, st = H.solve(P.B[:, 0], options=amg.opts(maxit=5000))
+    assert st == amg.AMG_OK
+    g = gold["aniso9_256x256_bootstrap"]
+    assert abs(info[0]["iters"] - g["iters"]) <= 1, (info[0]["iters"], g["iters"])
+    assert H.info()["n_level"] == g["levels"]
+    tr = np.linalg.norm(P.B[:, 0] - P.A @ x) / np.linalg.norm(P.B[:, 0])
+    assert tr <= 1.1e-8

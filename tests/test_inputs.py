@@ -144,3 +144,15 @@ def test_elasticity_spd_beyond_small_grids(N):
                    options=dict(SymmetricMode=True))
     assert np.array_equal(lu.perm_r, lu.perm_c)
     assert lu.U.diagonal().min() > 0
+
+
+def test_bootstrap_starts_and_stage_aggregator():
+    A = problems.aniso9(16)
+    s1 = inputs.bootstrap_starts(A.shape[0], 4)
+    s2 = inputs.bootstrap_starts(A.shape[0], 4)
+    assert len(s1) == 3 and all(np.array_equal(a, b) for a, b in zip(s1, s2))
+    assert not np.array_equal(s1[0], s1[1])
+    w = np.ones(A.shape[0])
+    aggs, nn = inputs.stage_aggregator(A, [2, 2])(w)
+    aggs2, nn2 = aggregation.aggregate_hierarchy(A, w, [2, 2])
+    assert nn == nn2 and all(np.array_equal(a, b) for a, b in zip(aggs, aggs2))
