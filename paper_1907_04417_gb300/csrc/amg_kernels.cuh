@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
 // registers (RMAX >= r_a coarse dofs), the row groups of the warp combined
 // by shuffles, then uc = D_c^{-1} fc.  No shared-memory tile and no CTA-wide
 // barrier; matrix and prolongator entries are read straight from global.
-template <typename TC, int K, int RMAX>
+template <typename TC, int K, int RMAX, bool STG>
 __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restrict__ row_start,
                                                    const int* __restrict__ coarse_start,
                                                    const long long* __restrict__ blk_start,
@@ -769,9 +769,12 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
   const int lane = threadIdx.x & 31;
   const int g = lane / CL, cl = lane % CL;
-  // the CTA's NWARP aggregates are one row range (staged when sg is enabled)
+  // STG: the CTA's NWARP aggregates are one row range, staged into shared
+  // memory first; otherwise the row loop reads global memory (a view fixed at
+  // compile time keeps its loads global and its offsets constant)
   const int a0 = blockIdx.x * NWARP, a1 = min(a0 + NWARP, nagg);
-  const CsrView<TC> cv = group_view<TC>(sg, smraw, __ldg(row_start + a0), __ldg(row_start + a1), rowptr, col, val);
+  CsrView<TC> cv{rowptr, 0, col, 0, val, 0};
+  if constexpr (STG) cv = group_view<TC>(sg, smraw, __ldg(row_start + a0), __ldg(row_start + a1), rowptr, col, val);
   const int a = a0 + (threadIdx.x >> 5);
   if (a >= nagg) return;  // whole warp
   const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
@@ -835,7 +838,7 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
 // group: CL lanes split the K columns (CPT each), JL lanes split the S
 // pattern columns (lane jl takes j = jl, jl + JL, ...) and are combined by
 // shuffles; there are 32 / (CL JL) slots per warp.
-constexpr int GATHER_G = 10;   // gathers in flight per lane in the grouped kernels
+constexpr int GATHER_G = 5;    // gathers in flight per lane in the grouped kernels
 constexpr int GROUPS_PER_CTA = 32;  // row groups of one grouped-sweep CTA
 
 template <typename TC, int K, int RA, int JL>
@@ -1015,7 +1018,8 @@ __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg,
                                                 const long long* __restrict__ blk_start, const TC* __restrict__ P,
                                                 const TC* __restrict__ uc, TC* __restrict__ u,
                                                 const int* __restrict__ done, int rows_max, int p_max,
-                                                int a_max) {
+                                                int a_max, const TC* __restrict__ f0,
+                                                const TC* __restrict__ dinv0) {
   if (*done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   TC* psm = reinterpret_cast<TC*>(smraw);
@@ -1050,7 +1054,15 @@ __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg,
     }
     TC* up = u + (size_t)(r0 + il) * K + c;
     TC uv[CPT];
-    ldp<TC, CPT>(up, uv);
+    if (f0) {  // u = D^{-1} f (the first pre-sweep from zero, not stored) before the correction
+      TC fv[CPT];
+      ldv<TC, CPT>(f0 + (size_t)(r0 + il) * K + c, fv);
+      const TC d = __ldg(dinv0 + r0 + il);
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) uv[q] = d * fv[q];
+    } else {
+      ldp<TC, CPT>(up, uv);
+    }
 #pragma unroll
     for (int q = 0; q < CPT; ++q) uv[q] += s[q];
     stv<TC, CPT>(up, uv);
@@ -1066,7 +1078,8 @@ __global__ void __launch_bounds__(BS) k_prolong_w(int nagg, const int* __restric
                                                   const int* __restrict__ coarse_start,
                                                   const long long* __restrict__ blk_start,
                                                   const TC* __restrict__ P, const TC* __restrict__ uc,
-                                                  TC* __restrict__ u, const int* __restrict__ done) {
+                                                  TC* __restrict__ u, const int* __restrict__ done,
+                                                  const TC* __restrict__ f0, const TC* __restrict__ dinv0) {
   if (*done) return;
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
   const int lane = threadIdx.x & 31, cl = lane % CL;
@@ -1094,8 +1107,20 @@ __global__ void __launch_bounds__(BS) k_prolong_w(int nagg, const int* __restric
       pv[0][p] = p < ra ? __ldg(Pa + (size_t)(i - rs) * ra + p) : TC(0);
       pv[1][p] = (two && p < ra) ? __ldg(Pa + (size_t)(i2 - rs) * ra + p) : TC(0);
     }
-    ldp<TC, CPT>(u + (size_t)i * K + cl * CPT, uv[0]);
-    if (two) ldp<TC, CPT>(u + (size_t)i2 * K + cl * CPT, uv[1]);
+    if (f0) {  // u = D^{-1} f (the first pre-sweep from zero, not stored) before the correction
+      TC fv[2][CPT];
+      ldv<TC, CPT>(f0 + (size_t)i * K + cl * CPT, fv[0]);
+      if (two) ldv<TC, CPT>(f0 + (size_t)i2 * K + cl * CPT, fv[1]);
+      const TC d0 = __ldg(dinv0 + i), d1 = two ? __ldg(dinv0 + i2) : TC(0);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        uv[0][t] = d0 * fv[0][t];
+        uv[1][t] = two ? d1 * fv[1][t] : TC(0);
+      }
+    } else {
+      ldp<TC, CPT>(u + (size_t)i * K + cl * CPT, uv[0]);
+      if (two) ldp<TC, CPT>(u + (size_t)i2 * K + cl * CPT, uv[1]);
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       // the same order as k_prolong: P_a row . uc, then added to u
@@ -1268,7 +1293,7 @@ __global__ void __launch_bounds__(BS) k_presmooth0(const int* __restrict__ cta_r
 //   z = u + D^{-1} (f - A u),
 // fused with r.z.  mode 0: rho = r.z (start); mode 1: beta = r.z / rho,
 // rho = r.z; mode 2: no scalars (a bare V-cycle).
-template <typename TC, int K, int NZL, bool DF>
+template <typename TC, int K, int NZL, bool DF, bool STG>
 __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                               const int* __restrict__ col, const TC* __restrict__ val,
                                               const TC* __restrict__ dinv, const TC* __restrict__ f,
@@ -1297,7 +1322,9 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
   // one row range per CTA, or (persistent launch, one system) every
   // gridDim.x-th range; float matrices are staged through the double-buffered
   // pipeline (the next range arrives while this one is processed)
-  constexpr bool PIPE = sizeof(TC) == 4;
+  // STG: the staged variants (a view fixed at compile time keeps the
+  // unstaged loads global with constant offsets)
+  constexpr bool PIPE = sizeof(TC) == 4 && STG;
   const bool piped = PIPE && sg.enabled;
   if (piped) {
     pipe_init(smraw);
@@ -1322,8 +1349,10 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
     int roff, joff;
     pipe_wait<1>(sg, smraw, it & 1, it >> 1, r0, rowptr, prp, roff, pcs, pv, joff);
     cv = CsrView<TC>{prp, roff, pcs, joff, reinterpret_cast<const TC*>(pv[0]), joff};
-  } else {
+  } else if constexpr (STG) {
     cv = staged_view<TC>(sg, smraw, r0, r1, rowptr, col, val);
+  } else {
+    cv = CsrView<TC>{rowptr, 0, col, 0, val, 0};
   }
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     int i = base + g;

@@ -91,9 +91,10 @@ template <typename TC>
 void launch_restrict(int K, int nzl, const Level& L, const Transfer& T, const TPart& tp, const Level& C,
                      bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, const int* done,
                      cudaStream_t st);
+// f0, dinv0 (optional): u starts from D^{-1} f0 instead of its stored value.
 template <typename TC>
 void launch_prolong(int K, const Transfer& T, const TPart& tp, const TC* uc, TC* u, const int* done,
-                    cudaStream_t st);
+                    cudaStream_t st, const TC* f0 = nullptr, const TC* dinv0 = nullptr);
 template <typename TC>
 void launch_coarse(int K, const Coarsest& C, const TC* f, TC* u, const int* done, cudaStream_t st);
 template <typename TC>
@@ -235,7 +236,7 @@ inline size_t csr_stage_bytes(const Stage& sg) {
           wsg.err = tp.sg.err;                                                                         \
           if (sizeof(TC) != 4 || tp.warp != 3) wsg.enabled = 0;                                        \
           const size_t wsm = pipe_bytes(wsg, 1, 1);                                                    \
-          auto kern = k_restrict_w<TC, KK, RM>;                                                        \
+          auto kern = wsg.enabled ? k_restrict_w<TC, KK, RM, true> : k_restrict_w<TC, KK, RM, false>;  \
           ensure_smem(kern, wsm);                                                                      \
           kern<<<(T.nagg + NWARP - 1) / NWARP, BS, wsm, st>>>(                                         \
               T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T), L.rowptr, L.col,         \
@@ -272,17 +273,17 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   }                                                                                                    \
   template <>                                                                                          \
   void launch_prolong<TC>(int K, const Transfer& T, const TPart& tp, const TC* uc, TC* u,             \
-                          const int* done, cudaStream_t st) {                                          \
+                          const int* done, cudaStream_t st, const TC* f0, const TC* dinv0) {           \
     if (tp.pwarp && tp.ra_max <= 8) {                                                                  \
       dispatch_k(K, [&](auto kc) {                                                                     \
         constexpr int KK = decltype(kc)::value;                                                        \
         const int grid = (T.nagg + NWARP - 1) / NWARP;                                                 \
         if (tp.ra_max <= 4)                                                                            \
           k_prolong_w<TC, KK, 4><<<grid, BS, 0, st>>>(T.nagg, T.row_start, T.coarse_start, T.blk_start, \
-                                                      pvals<TC>(T), uc, u, done);                      \
+                                                      pvals<TC>(T), uc, u, done, f0, dinv0);           \
         else                                                                                           \
           k_prolong_w<TC, KK, 8><<<grid, BS, 0, st>>>(T.nagg, T.row_start, T.coarse_start, T.blk_start, \
-                                                      pvals<TC>(T), uc, u, done);                      \
+                                                      pvals<TC>(T), uc, u, done, f0, dinv0);           \
       });                                                                                              \
       AMG_LAUNCH_CHECK();                                                                              \
       return;                                                                                          \
@@ -293,7 +294,8 @@ inline size_t csr_stage_bytes(const Stage& sg) {
       auto kern = k_prolong<TC, KK>;                                                                   \
       ensure_smem(kern, smem);                                                                         \
       kern<<<tp.ncta, BS, smem, st>>>(tp.cta_agg, T.row_start, T.coarse_start, T.blk_start,            \
-                                      pvals<TC>(T), uc, u, done, tp.rows_max, tp.p_max, tp.a_max);     \
+                                      pvals<TC>(T), uc, u, done, tp.rows_max, tp.p_max, tp.a_max, f0,  \
+                                      dinv0);                                                          \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \
@@ -319,7 +321,8 @@ inline size_t csr_stage_bytes(const Stage& sg) {
       dispatch_nzl(K, nzl, [&](auto nc) {                                                              \
         constexpr int NZ = decltype(nc)::value;                                                        \
         if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
-          auto kern = rlo ? k_post0<TC, KK, NZ, true> : k_post0<TC, KK, NZ, false>;                    \
+          auto kern = rlo ? (rp.sg.enabled ? k_post0<TC, KK, NZ, true, true> : k_post0<TC, KK, NZ, true, false>) \
+                          : (rp.sg.enabled ? k_post0<TC, KK, NZ, false, true> : k_post0<TC, KK, NZ, false, false>); \
           ensure_smem(kern, smem);                                                                     \
           kern<<<grid > 0 ? grid : rp.ncta, BS, smem, st>>>(rp.cta_row, L.rowptr, L.col, vals<TC>(L), \
                                                             dinvs<TC>(L), f, u, r, rlo, z, ks, mode,   \

@@ -47,7 +47,7 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
 // one non-zero ahead), and the p.q accumulators live in shared memory, one
 // slot per thread, so that three CTAs fit on an SM.  Offsets into the n x K
 // blocks are 32-bit (n K < 2^32 is checked on the host).
-template <int K, int NZL>
+template <int K, int NZL, bool STG>
 __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
                                                    const float* __restrict__ alo, const float* __restrict__ p,
@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
   // chunk; staged launches take col, val_hi and val_lo (and rowptr) through
   // the double-buffered pipeline, the next chunk arriving while this one is
   // processed
-  if (sg.enabled) {
+  // STG: staged launches (the unstaged variant keeps its loads global)
+  if (STG && sg.enabled) {
     pipe_init(smraw);
     if (threadIdx.x == 0 && (int)blockIdx.x < nchunk) {
       const float* v2[2] = {ahi, alo};
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
   const float* va = ahi;
   const float* vb = alo;
   int roff = 0, joff = 0;
-  if (sg.enabled) {
+  if (STG && sg.enabled) {
     const int nxt = chunk + gridDim.x;
     if (threadIdx.x == 0 && nxt < nchunk) {
       const float* v2[2] = {ahi, alo};
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
       }
     }
   }
-  if (sg.enabled) __syncthreads();  // the buffer is refilled two chunks on
+  if (STG && sg.enabled) __syncthreads();  // the buffer is refilled two chunks on
   }
   double d[CPT];
 #pragma unroll
@@ -367,8 +368,9 @@ __global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, co
 
 __device__ __forceinline__ void split2(double v, float& h, float& l) { df_split(v, h, l); }
 
-// r -= alpha q, ||r||^2; u0 = D^{-1} r_hi (first pre-sweep).  (x is
-// advanced by k_cg_p_df, which streams p anyway.)
+// r -= alpha q, ||r||^2; u0 = D^{-1} r_hi (the first pre-sweep from zero;
+// not stored when u0 is null, the cycle then folding it into A D^{-1}).
+// (x is advanced by k_cg_p_df, which streams p anyway.)
 template <int K>
 __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta_row, float* __restrict__ rh,
                                                      float* __restrict__ rl, const float* __restrict__ qh,
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
     ldp<float, CPT>(rl + e, rb);
     ldv<float, CPT>(qh + e, qa);
     ldv<float, CPT>(ql + e, qb);
-    float di = __ldg(dinv + e / K);
+    float di = u0 ? __ldg(dinv + e / K) : 0.f;
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
       df_mac(ah[t], al[t], qa[t], qb[t], ra[t], rb[t]);
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
     }
     stv<float, CPT>(rh + e, ra);
     stv<float, CPT>(rl + e, rb);
-    stv<float, CPT>(u0 + e, uo);
+    if (u0) stv<float, CPT>(u0 + e, uo);
   }
   }
   double d[CPT];
@@ -590,6 +592,7 @@ struct Workspace {
   Arena ar;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr, *b = nullptr;
   bool split = false;  // double-float CG vectors (float32-cycle mode)
+  bool u0free = false; // split with one pre-sweep: u0 = D^{-1} r_hi is folded into A D^{-1} (never stored)
   float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr;
   float *ph = nullptr, *qh = nullptr, *ql = nullptr;  // p is float32 (see k_cg_p_df)
   std::vector<void*> f, u, v;
@@ -1439,6 +1442,26 @@ static void ensure_groups(Plan& P) {
   }
 }
 
+// Level 0's column-scaled float copy A D^{-1} (fl32(a_ij / d_j)), made once
+// per plan for the u0-free float32 cycle; 16 padding elements like the
+// other non-zero arrays (the staging copies may read past a row range).
+__global__ void k_scale_cols(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ dinv, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) out[j] = (float)(val[j] * dinv[col[j]]);
+}
+
+static void ensure_scaled(Plan& P) {
+  Level& L = P.lev[0];
+  if (L.val_sc || !L.dinv64) return;
+  L.val_sc = P.arena->alloc<float>((size_t)L.nnz + 16);
+  AMG_CUDA(cudaMemset(L.val_sc + L.nnz, 0, 16 * sizeof(float)));
+  k_scale_cols<<<(L.n + 255) / 256, 256>>>(L.n, L.rowptr, L.col, L.val64, L.dinv64, L.val_sc);
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA(cudaDeviceSynchronize());
+}
+
 static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false) {
   long long key = ((long long)split << 40) | ((long long)K << 32) | ((long long)prec << 16) |
                   ((long long)pre << 8) | post;
@@ -1458,6 +1481,8 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   W->x = ar.alloc<double>(n0k);
   W->r = ar.alloc<double>(n0k);
   W->split = split;
+  W->u0free = split && pre == 1 && P.L > 1;
+  if (W->u0free) ensure_scaled(P);
   if (split) {
     for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
   } else {
@@ -1637,8 +1662,17 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     bool smooth_next = (k + 1 < L - 1);
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_RESTRICT_L0 : -1, st, pool);
-      launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], W.tp[k], P.lev[k + 1], smooth_next, F(k), cur[k],
-                          F(k + 1), cur[k + 1], done, st);
+      if (k == 0 && W.u0free) {
+        // t = f - A D^{-1} f: the first pre-sweep from zero is folded into the
+        // column-scaled matrix, so u0 = D^{-1} f is never stored
+        Level L0s = P.lev[0];
+        L0s.val32 = P.lev[0].val_sc;
+        launch_restrict<TC>(K, W.nzl[0], L0s, P.tr[0], W.tp[0], P.lev[1], smooth_next, F(0), F(0), F(1),
+                            cur[1], done, st);
+      } else {
+        launch_restrict<TC>(K, W.nzl[k], P.lev[k], P.tr[k], W.tp[k], P.lev[k + 1], smooth_next, F(k), cur[k],
+                            F(k + 1), cur[k + 1], done, st);
+      }
     }
   }
   launch_coarse<TC>(K, P.co, F(L - 1), cur[L - 1], done, st);
@@ -1646,7 +1680,10 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   for (int k = L - 2; k >= 0; --k) {
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_PROLONG_L0 : -1, st, pool);
-      launch_prolong<TC>(K, P.tr[k], W.tp[k], res, cur[k], done, st);
+      if (k == 0 && W.u0free)  // u = D^{-1} f + P e
+        launch_prolong<TC>(K, P.tr[0], W.tp[0], res, cur[0], done, st, F(0), reinterpret_cast<const TC*>(P.lev[0].dinv32));
+      else
+        launch_prolong<TC>(K, P.tr[k], W.tp[k], res, cur[k], done, st);
     }
     int sweeps = (k == 0) ? W.post - 1 : W.post;
     for (int s = 0; s < sweeps; ++s) {
@@ -1670,7 +1707,7 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
       dispatch_nzl(W.K, W.nzl_q, [&](auto nc) {
         constexpr int NZ = decltype(nc)::value;
         if constexpr (VT<float, KK>::CL * NZ <= 32) {
-          auto kern = k_cg_q_df<KK, NZ>;
+          auto kern = W.q_stage && W.rq.sg.enabled ? k_cg_q_df<KK, NZ, true> : k_cg_q_df<KK, NZ, false>;
           Stage sg = W.rq.sg;
           sg.enabled = sg.enabled && W.q_stage;
           size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
@@ -1738,7 +1775,7 @@ static void launch_update_df(Workspace& W, const Level& L, cudaStream_t st) {
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     k_cg_update_df<KK><<<W.upd_grid ? W.upd_grid : W.rp[0].ncta, BS, 0, st>>>(
-        W.rp[0].cta_row, W.rh, W.rl, W.qh, W.ql, L.dinv32, static_cast<float*>(W.u[0]),
+        W.rp[0].cta_row, W.rh, W.rl, W.qh, W.ql, L.dinv32, W.u0free ? nullptr : static_cast<float*>(W.u[0]),
         W.upd_grid ? W.ksf_upd : W.ks, W.rp[0].ncta);
   });
   AMG_LAUNCH_CHECK();
@@ -1776,7 +1813,7 @@ static void enqueue_start(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
       launch_pair(true, nk, W.x, W.xh, W.xl, nullptr, W.ks.done, st);
     }
     TC* f0 = (W.prec == 64 || W.split) ? nullptr : static_cast<TC*>(W.f[0]);
-    launch_presmooth0<TC>(W.K, L0, W.rp[0], W.r, static_cast<TC*>(W.u[0]), f0, W.ks.done, st);
+    if (!W.u0free) launch_presmooth0<TC>(W.K, L0, W.rp[0], W.r, static_cast<TC*>(W.u[0]), f0, W.ks.done, st);
     enqueue_cycle<TC>(h, P, W, st, 0, W.ks.done, W.ks, nullptr);
   }
   launch_cg_p(P, W, L0, 1, st);
