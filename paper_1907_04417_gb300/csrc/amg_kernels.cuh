@@ -608,13 +608,19 @@ __global__ void __launch_bounds__(BS) k_smooth(const int* __restrict__ cta_row, 
     int i = base + g;
     bool valid = i < r1;
     const size_t o = (size_t)i * K + cl * CPT;
-    TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
-    if (valid && nzl == 0) {
-      TC fv[CPT], uv[CPT], out[CPT];
+    // the row's own operands are requested before its gathers (a load after
+    // the gather loop would wait for it: one memory round trip per row pass)
+    TC fv[CPT], uv[CPT], di = TC(0);
+    const bool own = valid && nzl == 0;
+    if (own) {
       ldv<TC, CPT>(f + o, fv);
       ldv<TC, CPT>(u + o, uv);
-      TC di = __ldg(dinv + i);
+      di = __ldg(dinv + i);
+    }
+    TC acc[CPT];
+    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
+    if (own) {
+      TC out[CPT];
 #pragma unroll
       for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[t], uv[t]);
       stv<TC, CPT>(v + o, out);
@@ -1358,8 +1364,7 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
     int i = base + g;
     bool valid = i < r1;
     const size_t o = (size_t)i * K + cl * CPT;
-    TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
+    // the row's own operands are requested before its gathers
     TC fv[CPT], uv[CPT];
     float lv[NF];
     if (valid && nzl == 0) {
@@ -1367,6 +1372,8 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
       ldv<TC, CPT>(u + o, uv);
       if constexpr (DF) ldv<float, CPT>(rlo + o, lv);
     }
+    TC acc[CPT];
+    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
     if constexpr (DF) {
       if (valid && nzl == 0) {
         TC zt[CPT];
