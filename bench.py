@@ -185,10 +185,11 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the level-0 solve kernels (their
+    device code and launch choices); stored traffic counts only for them."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1907_04417_gb300", "csrc"))):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(ROOT, "paper_1907_04417_gb300", "csrc", f), "rb").read())
+    for f in ("amg_kernels.cuh", "amg_solve.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1907_04417_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
