@@ -190,6 +190,22 @@ amg_status amg_bootstrap_test(const amg_handle* hs, int32_t r, double* x, int32_
                               int32_t symmetric, const amg_opts* opts, void* stream, double* rho,
                               double* anorm);
 
+/*
+ * Compatible weighted matching of one pairwise aggregation step (Section 3)
+ * on the device.  For the graph of A (CSR, host or device; the pattern must
+ * be structurally symmetric, columns sorted) and a vector w (n float64, host
+ * or device) the edge weights are
+ *     c_ij = 1 - 2 a_ij w_i w_j / (a_ii w_i^2 + a_jj w_j^2)   (i < j, a_ij the
+ * stored upper entry), each float64 operation rounded on its own; only edges
+ * with c_ij > 0 take part.  The matching is the greedy matching on the strict
+ * order (c desc, smaller end asc, larger end asc), which approximates the
+ * maximum product matching of Section 3.  mate (n int32, host or device,
+ * output): the partner of every vertex, -1 if unmatched.  The call allocates
+ * its own work arrays and synchronises ``stream``.  A malformed or
+ * structurally non-symmetric pattern gives AMG_ERR_INVALID_ARG.
+ */
+amg_status amg_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate, void* stream);
+
 /* Hierarchy characteristics; never fails for a valid handle. */
 amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info);
 

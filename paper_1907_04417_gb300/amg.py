@@ -91,6 +91,7 @@ SIGNATURES = {
                                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "amg_bootstrap_test": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                      C.c_int32, C.POINTER(amg_opts), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amg_pairwise_matching": (C.c_int, [C.POINTER(amg_csr), C.c_void_p, C.c_void_p, C.c_void_p]),
     "amg_destroy": (None, [C.c_void_p]),
     "amg_last_error": (C.c_char_p, []),
 }
@@ -401,3 +402,20 @@ def bootstrap_test(hs, x, nu: int, symmetric: bool = True, options: amg_opts | N
                                     C.byref(options) if options is not None else None, _stream(stream),
                                     rho.ctypes.data, anorm.ctypes.data))
     return _reshape(x2, shape), rho, anorm
+
+
+def pairwise_matching(A, w, stream=None) -> np.ndarray:
+    """Compatible weighted matching of one pairwise step on the device
+    (amg_pairwise_matching in include/amg.h).  A: scipy CSR matrix; w: (n,)
+    float64.  Returns mate (n,) int32, -1 for unmatched vertices."""
+    keep = []
+    rowptr = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    n = int(A.shape[0])
+    csr = amg_csr(n, int(col.size), rowptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+    keep += [rowptr, col, val, wv]
+    mate = np.empty(n, dtype=np.int32)
+    _check(lib().amg_pairwise_matching(C.byref(csr), wv.ctypes.data, mate.ctypes.data, _stream(stream)))
+    return mate

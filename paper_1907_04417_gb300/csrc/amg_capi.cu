@@ -230,6 +230,14 @@ amg_status amg_bootstrap_test(const amg_handle* hs, int32_t r, double* x, int32_
   });
 }
 
+amg_status amg_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate, void* stream) {
+  if (!A || !w || !mate) return fail(AMG_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() -> amg_status {
+    amg::run_pairwise_matching(A, w, mate, as_stream(stream));
+    return AMG_OK;
+  });
+}
+
 amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info) {
   if (!h || !info) return fail(AMG_ERR_INVALID_ARG, "null argument");
   std::memset(info, 0, sizeof(*info));

@@ -221,6 +221,9 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
 void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* x_caller,
                       int nrhs, double* grad, cudaStream_t st);
 
+// compatible weighted matching of one pairwise step (amg_matching.cu)
+void run_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate, cudaStream_t st);
+
 // bootstrap testing phase (amg_bootstrap.cu)
 void run_bootstrap_test(const std::vector<amg_hierarchy*>& hs, double* x, int nrhs, int nu, int symmetric,
                         const amg_opts& o, cudaStream_t st, double* rho, double* anorm);
