@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Time to a 1e-8 relative residual per right-hand side for the AMG-PCG
 solve of the rotated anisotropic diffusion problem (eps = 1e-3, theta =
-pi/6, 9-point, 1024 x 1024, 4 smooth vectors, aggregates of 16, 5 levels).
+pi/6, 9-point, 1024 x 1024, 4 smooth vectors from the seeded bootstrap of
+Algorithm 1, aggregates of 16, 5 levels).
 
-One step = one complete batched solve (float32 V-cycle inside float64 CG)
-of ``--batch`` seeded uniform[-1, 1] right-hand sides from a zero initial
-guess, with inputs resident in HBM.  The plain float64 solve of one RHS is
-timed beside it.  Prints one JSON line (rank 0).
+One step = one complete batched solve (float32 V-cycle inside CG whose
+vectors are double-float pairs and whose scalars are float64) of ``--batch``
+seeded uniform[-1, 1] right-hand sides from a zero initial guess, with inputs
+resident in HBM.  The plain float64 solve of one RHS is timed beside it.  The
+bootstrap (testing phase on the device) and the setup are not timed.  Prints
+one JSON line (rank 0).
 
     python bench.py [--gpus N --steps K --warmup W --impl gb300|reference]
 
