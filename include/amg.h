@@ -206,6 +206,27 @@ amg_status amg_bootstrap_test(const amg_handle* hs, int32_t r, double* x, int32_
  */
 amg_status amg_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate, void* stream);
 
+/*
+ * One whole pairwise aggregation step (Section 3) on the device: the matching
+ * of amg_pairwise_matching; the aggregates (each pair or singleton is
+ * numbered by its smallest member, in increasing order); the pairwise
+ * prolongator of Eq. (prol) with one column per aggregate ([w_i, w_j] /
+ * sqrt(w_i^2 + w_j^2) for a pair, w_k/|w_k| for a singleton, 1 when w_k = 0,
+ * equal weights for a pair with w = 0); the coarse vector w_c = P^T w; the
+ * next graph A_c = P^T A P in CSR with sorted columns.
+ * Outputs (host or device, capacities from A):
+ *   agg[n]          aggregate of every vertex;
+ *   nc              number of aggregates (one int32, host);
+ *   rowptr_c[n+1], col_c[nnz(A)], val_c[nnz(A)]   A_c (nc + 1 and nnz_c used);
+ *   nnz_c           entries of A_c (one int32, host);
+ *   wc[n]           w_c (nc used).
+ * The call allocates its own work arrays and synchronises ``stream``.  A
+ * malformed or structurally non-symmetric A gives AMG_ERR_INVALID_ARG, as
+ * does a coarse row of more than 256 entries before merging.
+ */
+amg_status amg_pairwise_step(const amg_csr* A, const double* w, int32_t* agg, int32_t* nc, int32_t* rowptr_c,
+                             int32_t* col_c, double* val_c, int32_t* nnz_c, double* wc, void* stream);
+
 /* Hierarchy characteristics; never fails for a valid handle. */
 amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info);
 

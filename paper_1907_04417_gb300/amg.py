@@ -92,6 +92,9 @@ SIGNATURES = {
     "amg_bootstrap_test": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                      C.c_int32, C.POINTER(amg_opts), C.c_void_p, C.c_void_p, C.c_void_p]),
     "amg_pairwise_matching": (C.c_int, [C.POINTER(amg_csr), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "amg_pairwise_step": (C.c_int, [C.POINTER(amg_csr), C.c_void_p, C.c_void_p, C.POINTER(C.c_int32),
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p,
+                                    C.c_void_p]),
     "amg_destroy": (None, [C.c_void_p]),
     "amg_last_error": (C.c_char_p, []),
 }
@@ -419,3 +422,48 @@ def pairwise_matching(A, w, stream=None) -> np.ndarray:
     mate = np.empty(n, dtype=np.int32)
     _check(lib().amg_pairwise_matching(C.byref(csr), wv.ctypes.data, mate.ctypes.data, _stream(stream)))
     return mate
+
+
+def pairwise_step(A, w, stream=None):
+    """One pairwise aggregation step on the device (amg_pairwise_step in
+    include/amg.h).  A: scipy CSR matrix; w: (n,) float64.  Returns (agg,
+    A_c, w_c) with agg (n,) int32, A_c a scipy CSR matrix and w_c (nc,)."""
+    import scipy.sparse as sp
+    rowptr = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    n, nnz = int(A.shape[0]), int(col.size)
+    csr = amg_csr(n, nnz, rowptr.ctypes.data, col.ctypes.data, val.ctypes.data)
+    agg = np.empty(n, dtype=np.int32)
+    rpc = np.empty(n + 1, dtype=np.int32)
+    colc = np.empty(max(nnz, 1), dtype=np.int32)
+    valc = np.empty(max(nnz, 1), dtype=np.float64)
+    wc = np.empty(max(n, 1), dtype=np.float64)
+    nc = C.c_int32()
+    nnzc = C.c_int32()
+    _check(lib().amg_pairwise_step(C.byref(csr), wv.ctypes.data, agg.ctypes.data, C.byref(nc), rpc.ctypes.data,
+                                   colc.ctypes.data, valc.ctypes.data, C.byref(nnzc), wc.ctypes.data,
+                                   _stream(stream)))
+    k, z = nc.value, nnzc.value
+    Ac = sp.csr_matrix((valc[:z].copy(), colc[:z].copy(), rpc[:k + 1].copy()), shape=(k, k))
+    return agg, Ac, wc[:k].copy()
+
+
+def aggregate_hierarchy(A, w, steps_per_level, min_nodes: int = 1):
+    """Nested aggregate maps from composed pairwise steps, every step on the
+    device (the composition of Section 3, aggressive coarsening): aggs[k][node]
+    is the level-(k+1) aggregate of level-k node, n_nodes[k] the level-k node
+    count."""
+    aggs, n_nodes = [], [A.shape[0]]
+    Ak, wk = A, np.asarray(w, dtype=np.float64)
+    for s in steps_per_level:
+        comp = np.arange(Ak.shape[0])
+        for _ in range(s):
+            if Ak.shape[0] <= min_nodes:
+                break
+            agg, Ak, wk = pairwise_step(Ak, wk)
+            comp = agg[comp]
+        aggs.append(comp.astype(np.int32))
+        n_nodes.append(int(Ak.shape[0]))
+    return aggs, n_nodes

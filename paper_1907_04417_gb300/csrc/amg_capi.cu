@@ -238,6 +238,16 @@ amg_status amg_pairwise_matching(const amg_csr* A, const double* w, int32_t* mat
   });
 }
 
+amg_status amg_pairwise_step(const amg_csr* A, const double* w, int32_t* agg, int32_t* nc, int32_t* rowptr_c,
+                             int32_t* col_c, double* val_c, int32_t* nnz_c, double* wc, void* stream) {
+  if (!A || !w || !agg || !nc || !rowptr_c || !col_c || !val_c || !nnz_c || !wc)
+    return fail(AMG_ERR_INVALID_ARG, "null argument");
+  return guarded([&]() -> amg_status {
+    amg::run_pairwise_step(A, w, agg, nc, rowptr_c, col_c, val_c, nnz_c, wc, as_stream(stream));
+    return AMG_OK;
+  });
+}
+
 amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info) {
   if (!h || !info) return fail(AMG_ERR_INVALID_ARG, "null argument");
   std::memset(info, 0, sizeof(*info));

@@ -223,6 +223,8 @@ void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* 
 
 // compatible weighted matching of one pairwise step (amg_matching.cu)
 void run_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate, cudaStream_t st);
+void run_pairwise_step(const amg_csr* A, const double* w, int32_t* agg, int32_t* nc, int32_t* rowptr_c,
+                       int32_t* col_c, double* val_c, int32_t* nnz_c, double* wc, cudaStream_t st);
 
 // bootstrap testing phase (amg_bootstrap.cu)
 void run_bootstrap_test(const std::vector<amg_hierarchy*>& hs, double* x, int nrhs, int nu, int symmetric,

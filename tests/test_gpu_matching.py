@@ -78,3 +78,33 @@ def test_matching_rejects_non_symmetric_pattern(amg):
     with pytest.raises(amg.AMGError) as e:
         amg.pairwise_matching(A, np.ones(3))
     assert e.value.status == amg.AMG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name", GRAPHS)
+@pytest.mark.parametrize("wkind", ["ones", "random"])
+def test_pairwise_step_matches_host(amg, name, wkind):
+    """One step from the same (A, w): aggregates and the coarse pattern index
+    for index, A_c and w_c to rounding (the sums run in another order)."""
+    A = sp.csr_matrix(_graphs()[name])
+    A.sort_indices()
+    n = A.shape[0]
+    w = np.ones(n) if wkind == "ones" else np.random.default_rng(n + 1).standard_normal(n)
+    agg, Ac, wc = amg.pairwise_step(A, w)
+    agg_h, Ac_h, wc_h = aggregation.pairwise_step(A, w)
+    np.testing.assert_array_equal(agg, agg_h)
+    np.testing.assert_array_equal(Ac.indptr, Ac_h.indptr)
+    np.testing.assert_array_equal(Ac.indices, Ac_h.indices)
+    np.testing.assert_allclose(Ac.data, Ac_h.data, rtol=1e-12, atol=1e-13 * np.abs(Ac_h.data).max())
+    np.testing.assert_allclose(wc, wc_h, rtol=1e-13, atol=1e-14 * np.abs(wc_h).max())
+
+
+def test_composed_steps_match_host(amg):
+    """Four levels of composed steps entirely on the device (random vector, so
+    no two edge weights tie) against the host composition."""
+    A = problems.aniso9(64)
+    w = np.random.default_rng(9).standard_normal(A.shape[0])
+    aggs, nn = amg.aggregate_hierarchy(A, w, [2, 2, 2])
+    aggs_h, nn_h = aggregation.aggregate_hierarchy(A, w, [2, 2, 2])
+    assert nn == nn_h
+    for a, b in zip(aggs, aggs_h):
+        np.testing.assert_array_equal(a, b)
