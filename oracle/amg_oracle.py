@@ -30,6 +30,15 @@ the paper states the steps.  Readings of points the paper leaves open:
   (the paper uses a sparse LU; the result is the same exact solve).
 * PCG (Section 5): zero initial guess, stop when the recursive residual
   satisfies ||r||_2 <= rtol ||b||_2, Fletcher-Reeves beta.
+* Cycle variants (Section 5 names K-cycles with two inner flexible-CG
+  iterations and forward/backward Gauss-Seidel as the smoother of the
+  bootstrap's hierarchies): Gauss-Seidel visits the rows colour by colour,
+  the colours from a greedy colouring in decreasing priority
+  (splitmix64(i), i) of the row index i in the numbering above (the paper's
+  sweep is lexicographic); the inner flexible CG keeps one previous
+  direction and always runs two iterations; a column whose step
+  denominator is zero takes no step.  The outer PCG keeps the
+  Fletcher-Reeves beta for the K-cycle too.
 """
 from __future__ import annotations
 
@@ -326,3 +335,180 @@ def bootstrap(A, w0, m: int, nu: int, aggregate, starts, symmetric: bool = True,
         W[:, r] = x / a_norm(A, x)[0]
         rhos.append(float(rho[0]))
     return W, rhos
+
+
+# --------------------------------------------------------------------------
+# cycle variants (Section 5): forward/backward Gauss-Seidel smoothing, here
+# in multicolour order, and the K-cycle with two inner flexible-CG
+# iterations on every level but the coarsest
+# --------------------------------------------------------------------------
+
+def splitmix64(i):
+    """SplitMix64 (Steele, Lea & Flood, OOPSLA 2014; Vigna's splitmix64.c)
+    output for state i: the state plus the golden-ratio increment
+    0x9e3779b97f4a7c15, then the finaliser z ^= z >> 30, z *= 0xbf58476d1ce4e5b9,
+    z ^= z >> 27, z *= 0x94d049bb133111eb, z ^= z >> 31, all mod 2^64.
+    Vectorised over integer arrays (uint64 result)."""
+    z = np.atleast_1d(np.asarray(i)).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = z + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def priority_rank(n: int) -> np.ndarray:
+    """rank[i] = position of vertex i in the increasing order of the keys
+    (splitmix64(i), i); a larger rank is a higher priority."""
+    idx = np.arange(n)
+    order = np.lexsort((idx, splitmix64(idx)))
+    rank = np.empty(n, dtype=np.int64)
+    rank[order] = idx
+    return rank
+
+
+def greedy_colouring(A: sp.csr_matrix) -> np.ndarray:
+    """Greedy colouring of the graph of A (its stored off-diagonal pattern)
+    in decreasing priority order: every vertex takes the smallest colour that
+    none of its higher-priority neighbours holds.  Computed in rounds: a
+    vertex is coloured in the round in which all its higher-priority
+    neighbours are coloured, which gives the same colours as visiting the
+    vertices one by one in priority order (a vertex's colour depends only on
+    its higher-priority neighbours)."""
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    cols = A.indices
+    off = rows != cols
+    rows, cols = rows[off], cols[off]
+    rank = priority_rank(n)
+    higher = rank[cols] > rank[rows]
+    hr, hc = rows[higher], cols[higher]          # edges to higher-priority neighbours
+    deg = np.bincount(hr, minlength=n)
+    colour = np.full(n, -1, dtype=np.int64)
+    while np.any(colour < 0):
+        waiting = np.bincount(hr[colour[hc] < 0], minlength=n)
+        ready = np.flatnonzero((colour < 0) & (waiting == 0))
+        width = int(deg[ready].max(initial=0)) + 2
+        slot = np.full(n, -1, dtype=np.int64)
+        slot[ready] = np.arange(ready.size)
+        used = np.zeros((ready.size, width), dtype=bool)
+        e = slot[hr] >= 0
+        c = colour[hc[e]]
+        keep = c < width
+        used[slot[hr[e]][keep], c[keep]] = True
+        colour[ready] = np.argmin(used, axis=1)
+    return colour
+
+
+def gs_sweep(A: sp.csr_matrix, diag, colour, f, u, backward: bool = False):
+    """One multicolour Gauss-Seidel sweep: colours in increasing order
+    (forward) or decreasing order (backward); within a colour every row i
+    becomes u_i + (f_i - (A u)_i) / a_ii with the current u (rows of one
+    colour share no edge, so their order is immaterial)."""
+    u = np.array(u, dtype=np.float64)
+    d = diag if np.ndim(f) == 1 else diag[:, None]
+    ncol = int(colour.max()) + 1 if colour.size else 0
+    seq = range(ncol - 1, -1, -1) if backward else range(ncol)
+    for c in seq:
+        S = np.flatnonzero(colour == c)
+        u[S] = u[S] + (f[S] - A[S] @ u) / d[S]
+    return u
+
+
+def gs_data(H: Hierarchy):
+    """Colours and diagonals of the smoothed levels (cached on H)."""
+    if getattr(H, "_gs", None) is None:
+        H._gs = [(greedy_colouring(l.A), l.A.diagonal().copy()) for l in H.levels[:-1]]
+    return H._gs
+
+
+def _cdot(x, y):
+    """Column-wise inner products (a scalar for vectors)."""
+    return np.sum(x * y, axis=0)
+
+
+def fcg(A, r, precond, iters: int = 2):
+    """Flexible CG (Notay 2000) on A e = r from e = 0, each new direction
+    A-orthogonalised against the previous one only, ``iters`` iterations.
+    Columns of r are independent problems.  A zero denominator (a column
+    that has already converged exactly) contributes no step."""
+    r = np.array(r, dtype=np.float64)
+    e = np.zeros_like(r)
+    d_prev = Ad_prev = dAd_prev = None
+    for _ in range(iters):
+        c = precond(r)
+        Ac = A @ c
+        d, Ad = c, Ac
+        if d_prev is not None:
+            with np.errstate(divide="ignore", invalid="ignore"):
+                g = np.where(dAd_prev > 0, _cdot(c, Ad_prev) / dAd_prev, 0.0)
+            d = c - g * d_prev
+            Ad = Ac - g * Ad_prev
+        dAd = _cdot(d, Ad)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            alpha = np.where(dAd > 0, _cdot(d, r) / dAd, 0.0)
+        e = e + alpha * d
+        r = r - alpha * Ad
+        d_prev, Ad_prev, dAd_prev = d, Ad, dAd
+    return e
+
+
+def cycle(H: Hierarchy, f, k: int = 0, pre: int = 1, post: int = 1,
+          smoother: str = "l1jacobi", kind: str = "V"):
+    """One multigrid cycle on level k (Section 5 variants).
+
+    smoother "l1jacobi": the V-cycle smoother above (first sweep from zero
+    u = f / d).  smoother "gs": u starts at zero, ``pre`` forward multicolour
+    Gauss-Seidel sweeps before the coarse correction and ``post`` backward
+    sweeps after it (forward/backward GS as pre-/post-smoother, which keeps
+    the preconditioner symmetric).
+
+    kind "V": the coarse correction is one cycle on level k+1.  kind "K":
+    on every level k+1 but the coarsest the correction is two flexible-CG
+    iterations on A^{k+1} e = P^T (f - A u), each preconditioned by one
+    cycle on level k+1 (the K-cycle, a nonlinear AMLI cycle)."""
+    if k == H.L - 1:
+        return coarse_solve(H, f)
+    A = H.levels[k].A
+    P = H.levels[k + 1].P
+    if smoother == "l1jacobi":
+        d = H.levels[k].d if np.ndim(f) == 1 else H.levels[k].d[:, None]
+        u = f / d
+        for _ in range(pre - 1):
+            u = u + (f - A @ u) / d
+    elif smoother == "gs":
+        colour, dg = gs_data(H)[k]
+        u = np.zeros_like(np.asarray(f, dtype=np.float64))
+        for _ in range(pre):
+            u = gs_sweep(A, dg, colour, f, u)
+    else:
+        raise ValueError(smoother)
+    fc = P.T @ (f - A @ u)
+    inner = lambda g: cycle(H, g, k + 1, pre, post, smoother, kind)  # noqa: E731
+    if kind == "K" and k + 1 < H.L - 1:
+        e = fcg(H.levels[k + 1].A, fc, inner, 2)
+    elif kind in ("V", "K"):
+        e = inner(fc)
+    else:
+        raise ValueError(kind)
+    u = u + P @ e
+    for _ in range(post):
+        if smoother == "l1jacobi":
+            u = u + (f - A @ u) / d
+        else:
+            u = gs_sweep(A, dg, colour, f, u, backward=True)
+    return u
+
+
+def solve_variant(H: Hierarchy, b, rtol=1e-8, maxit=1000, fixed_iters=None, pre=1, post=1,
+                  smoother="l1jacobi", kind="V"):
+    """PCG (the same Fletcher-Reeves loop as ``solve``) preconditioned by one
+    ``cycle`` per iteration; returns (X, results)."""
+    A = H.levels[0].A
+    B = np.asarray(b, dtype=np.float64)
+    cols = B[:, None] if B.ndim == 1 else B
+    pc = lambda r: cycle(H, r, 0, pre, post, smoother, kind)  # noqa: E731
+    res = [pcg(A, cols[:, c], pc, rtol, maxit, fixed_iters=fixed_iters) for c in range(cols.shape[1])]
+    X = np.stack([r.x for r in res], axis=1)
+    return (X[:, 0] if B.ndim == 1 else X), res
