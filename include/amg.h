@@ -71,6 +71,17 @@ typedef struct {
                               error-free products and sums, about 2^-44 relative
                               accuracy) on the float32 pipes; 1: float64 FMAs.
                               The CG recurrences and dots stay float64 either way. 0 */
+  int32_t smoother;        /* 0: l1-Jacobi.  1: Gauss-Seidel, forward sweeps before
+                              and backward sweeps after the coarse correction
+                              (Section 5), rows visited colour by colour in a
+                              greedy colouring of each level's graph.  Needs
+                              cycle_precision 64 and a single hierarchy.        0 */
+  int32_t cycle;           /* 0: V-cycle.  1: K-cycle: on every level but the
+                              coarsest the coarse correction is two flexible-CG
+                              iterations preconditioned by the cycle one level
+                              down (Section 5; nonlinear, so the outer CG sees a
+                              slightly variable preconditioner).  Needs
+                              cycle_precision 64 and a single hierarchy.        0 */
 } amg_opts;
 
 /* Per right-hand-side result. */
@@ -164,8 +175,9 @@ amg_status amg_adjoint(amg_handle h, const double* g, const double* x, int32_t n
                        double* lambda, double* grad_val, const amg_opts* opts,
                        void* stream, amg_info* info);
 
-/* Apply the preconditioner once, z = B r (one V-cycle, Section 5), in the
- * precision opts->cycle_precision.  r, z: n x nrhs row-major float64. */
+/* Apply the preconditioner once, z = B r (one V-cycle, Section 5, or the
+ * variant that opts->smoother and opts->cycle select), in the precision
+ * opts->cycle_precision.  r, z: n x nrhs row-major float64. */
 amg_status amg_vcycle(amg_handle h, const double* r, double* z, int32_t nrhs,
                       const amg_opts* opts, void* stream);
 
@@ -247,6 +259,20 @@ amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info);
 amg_status amg_export_level(amg_handle h, int32_t k, int64_t* sizes, int32_t* rowptr,
                             int32_t* col, double* val, int32_t* perm, int32_t* agg_id,
                             int32_t* r, int32_t* row_start, double* pval);
+
+/*
+ * Colours of the Gauss-Seidel smoother on level k (0 <= k <= levels-2), for
+ * inspection and tests.  The rows of each level are coloured greedily in
+ * decreasing priority (splitmix64(i), i), i the row in the caller's
+ * numbering (level 0: the caller's dofs; coarse levels: dofs numbered
+ * aggregate by aggregate in aggregate-index order, an aggregate's kept
+ * columns in descending singular-value order): every row takes the smallest
+ * colour that none of its higher-priority neighbours in the graph of A^k
+ * holds.  colour (n_k int32, host, may be NULL) receives them in that
+ * numbering and *ncolours (may be NULL) their number.  The first call builds
+ * the colouring on the device (it is kept with the hierarchy).
+ */
+amg_status amg_level_colours(amg_handle h, int32_t k, int32_t* colour, int32_t* ncolours);
 
 /* Kernel timing hook used by the benchmark: while enabled, every launch of
  * the kernel family ``kernel_id`` (AMG_KERNEL_*) is bracketed by CUDA events

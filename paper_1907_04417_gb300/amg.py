@@ -49,7 +49,12 @@ class amg_opts(C.Structure):
     _fields_ = [("tol_svd", C.c_double), ("pre", C.c_int32), ("post", C.c_int32),
                 ("cycle_precision", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32),
                 ("use_graph", C.c_int32), ("check_every", C.c_int32), ("autotune", C.c_int32),
-                ("outer_fp64", C.c_int32)]
+                ("outer_fp64", C.c_int32), ("smoother", C.c_int32), ("cycle", C.c_int32)]
+
+SMOOTHER_L1JACOBI = 0
+SMOOTHER_GS = 1
+CYCLE_V = 0
+CYCLE_K = 1
 
 
 class amg_info(C.Structure):
@@ -84,6 +89,7 @@ SIGNATURES = {
     "amg_export_level": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p]),
+    "amg_level_colours": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
     "amg_timer_enable": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "amg_timer_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "amg_kernel_launches": (C.c_int, [C.POINTER(C.c_int64)]),
@@ -276,6 +282,15 @@ class Hierarchy:
         return {"levels": L, "m": hi.m, "opc": hi.opc, "cr": hi.cr,
                 "n_level": list(hi.n_level[:L]), "nnz_level": list(hi.nnz_level[:L]),
                 "truncated_aggs": hi.truncated_aggs, "device_bytes": hi.device_bytes}
+
+    def level_colours(self, k: int):
+        """(colour, ncolours) of the Gauss-Seidel smoother on level k, the
+        colours in the caller's numbering of that level."""
+        n = self.info()["n_level"][k]
+        colour = np.zeros(max(n, 1), np.int32)
+        nc = C.c_int32()
+        _check(lib().amg_level_colours(self.h, k, colour.ctypes.data, C.byref(nc)))
+        return colour[:n], nc.value
 
     def export_level(self, k: int) -> dict:
         sizes = np.zeros(6, dtype=np.int64)

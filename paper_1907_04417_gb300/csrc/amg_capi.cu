@@ -54,6 +54,8 @@ void amg_default_opts(amg_opts* o) {
   o->check_every = 8;
   o->autotune = 1;
   o->outer_fp64 = 0;
+  o->smoother = 0;
+  o->cycle = 0;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -267,6 +269,15 @@ amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info) {
   info->truncated_aggs = h->truncated;
   info->device_bytes = (int64_t)P.arena->bytes;
   return AMG_OK;
+}
+
+amg_status amg_level_colours(amg_handle h, int32_t k, int32_t* colour, int32_t* ncolours) {
+  if (!h) return fail(AMG_ERR_INVALID_ARG, "null handle");
+  return guarded([&]() -> amg_status {
+    int nc = amg::level_colours(h, k, colour, h->own);
+    if (ncolours) *ncolours = nc;
+    return AMG_OK;
+  });
 }
 
 amg_status amg_export_level(amg_handle h, int32_t k, int64_t* sizes, int32_t* rowptr, int32_t* col, double* val,

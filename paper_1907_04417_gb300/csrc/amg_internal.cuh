@@ -169,6 +169,12 @@ struct Plan {
   std::unique_ptr<Arena> arena;
   std::map<long long, std::shared_ptr<Workspace>> ws;
   bool groups_done = false;    // row groups of the coarse levels detected
+  // multicolour Gauss-Seidel (smoothed levels): colour and diagonal of every
+  // row, number of colours; built on first use (amg_variants.cu)
+  bool gs_done = false;
+  std::vector<int*> gs_colour;
+  std::vector<double*> gs_diag;
+  std::vector<int> gs_ncol;
   Plan() : arena(new Arena) {}
   ~Plan();
 };
@@ -225,6 +231,30 @@ void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* 
 void run_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate, cudaStream_t st);
 void run_pairwise_step(const amg_csr* A, const double* w, int32_t* agg, int32_t* nc, int32_t* rowptr_c,
                        int32_t* col_c, double* val_c, int32_t* nnz_c, double* wc, cudaStream_t st);
+
+// cycle variants (amg_variants.cu): the buffers and launch choices of one
+// float64 solve workspace that the variant cycle reads.  smoother 0 is
+// l1-Jacobi, 1 multicolour forward/backward Gauss-Seidel; kind 0 is the
+// V-cycle, 1 the K-cycle (two flexible-CG iterations on every level but the
+// coarsest).
+struct VarCycle {
+  int smoother = 0, kind = 0, K = 0, pre = 1, post = 1;
+  std::vector<double*> f, u, v;              // per level (f[0] is the CG residual)
+  std::vector<double*> c2, v1, v2, r2, e;    // K-cycle buffers of levels 1..L-2
+  std::vector<int> nzl;
+  std::vector<RPart> rp;
+  std::vector<TPart> tp;
+  double* partial = nullptr;                 // per-CTA partial inner products
+  std::vector<double*> dots;                 // per level: 5 K inner products
+  int dot_rows = 1024;                       // rows per CTA of the inner products
+};
+void ensure_gs(amg_hierarchy* h, Plan& P, cudaStream_t st);
+size_t var_level_ctas(int n, const VarCycle& vc);
+// z = B r (level 0, float64) by one variant cycle; u0 is level-0 scratch.
+void enqueue_var_cycle(const Plan& P, const VarCycle& vc, const double* r, double* z, double* u0,
+                       const int* done, cudaStream_t st);
+// colours of level k in the caller's numbering (the oracle's dof order)
+int level_colours(amg_hierarchy* h, int k, int32_t* colour, cudaStream_t st);
 
 // bootstrap testing phase (amg_bootstrap.cu)
 void run_bootstrap_test(const std::vector<amg_hierarchy*>& hs, double* x, int nrhs, int nu, int symmetric,

@@ -628,6 +628,8 @@ struct Workspace {
   long long gkernels = 0;
   int* h_iter = nullptr;  // pinned
   double grtol = -1;
+  int variant = 0;        // smoother | cycle << 1 (float64 only); 0: the tuned V-cycle
+  VarCycle var;           // buffers of the variant cycle
   std::vector<cudaEvent_t> gev;
   ~Workspace() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -1492,9 +1494,12 @@ static void ensure_scaled(Plan& P) {
   AMG_CUDA(cudaDeviceSynchronize());
 }
 
-static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false) {
-  long long key = ((long long)split << 40) | ((long long)K << 32) | ((long long)prec << 16) |
-                  ((long long)pre << 8) | post;
+static void make_var(Plan& P, Workspace& W, int variant);
+
+static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false,
+                         int variant = 0) {
+  long long key = ((long long)variant << 44) | ((long long)split << 40) | ((long long)K << 32) |
+                  ((long long)prec << 16) | ((long long)pre << 8) | post;
   auto it = P.ws.find(key);
   if (it != P.ws.end()) return *it->second;
   ensure_groups(P);
@@ -1618,8 +1623,40 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     out.insert(out.end(), {(long long)W->t_pu, (long long)W->t_pp, (long long)W->t_ppost, 0LL});
     tune_cache_store(tkey, out);
   }
+  if (variant) make_var(P, *W, variant);
   P.ws[key] = W;
   return *W;
+}
+
+// Buffers of the variant cycle: the workspace's level vectors, its tuned
+// launch choices and, for the K-cycle, five more vectors per inner level.
+static void make_var(Plan& P, Workspace& W, int variant) {
+  AMG_REQUIRE(W.prec == 64 && !W.split, "internal: variant cycles run in float64");
+  VarCycle& vc = W.var;
+  W.variant = variant;
+  vc.smoother = variant & 1;
+  vc.kind = (variant >> 1) & 1;
+  vc.K = W.K;
+  vc.pre = W.pre;
+  vc.post = W.post;
+  for (int k = 0; k < P.L; ++k) {
+    vc.f.push_back(static_cast<double*>(W.f[k]));
+    vc.u.push_back(static_cast<double*>(W.u[k]));
+    vc.v.push_back(static_cast<double*>(W.v[k]));
+  }
+  vc.nzl = W.nzl;
+  vc.rp = W.rp;
+  vc.tp = W.tp;
+  for (auto* b : {&vc.c2, &vc.v1, &vc.v2, &vc.r2, &vc.e}) b->assign(P.L, nullptr);
+  vc.dots.assign(P.L, nullptr);
+  size_t ncta_max = 1;
+  for (int j = 1; j + 1 < P.L && vc.kind == 1; ++j) {
+    const size_t nk = (size_t)P.lev[j].n * W.K;
+    for (auto* b : {&vc.c2, &vc.v1, &vc.v2, &vc.r2, &vc.e}) (*b)[j] = W.ar.alloc<double>(nk);
+    vc.dots[j] = W.ar.alloc<double>((size_t)5 * W.K);
+    ncta_max = std::max(ncta_max, var_level_ctas(P.lev[j].n, vc));
+  }
+  vc.partial = W.ar.alloc<double>(ncta_max * 2 * W.K);
 }
 
 // ------------------------------------------------------------- timing --
@@ -1835,6 +1872,9 @@ static void enqueue_start(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   if (P.L == 1) {
     enqueue_cycle<TC>(h, P, W, st, 0, W.ks.done, W.ks, nullptr);
     launch_rz(W, L0, 0, st);
+  } else if (W.variant) {
+    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.ks.done, st);
+    launch_rz(W, L0, 0, st);
   } else {
     if (W.split) {
       // x and r enter the double-float pairs; r_hi is the cycle's f0
@@ -1860,12 +1900,17 @@ static void enqueue_iteration(amg_hierarchy* h, Plan& P, Workspace& W, cudaStrea
   TC* f0 = (W.prec == 64 || P.L == 1) ? nullptr : static_cast<TC*>(W.f[0]);
   {
     TimedLaunch tl(h, AMG_KERNEL_CG_UPDATE, st, pool);
-    TC* u0 = P.L == 1 ? nullptr : static_cast<TC*>(W.u[0]);
+    TC* u0 = (P.L == 1 || W.variant) ? nullptr : static_cast<TC*>(W.u[0]);
     if (W.split) launch_update_df(W, L0, st);
     else launch_update<TC>(W.K, L0, W.rp[0], W.x, W.r, W.p, W.q, u0, f0, W.ks, st);
   }
-  enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
-  if (P.L == 1) launch_rz(W, L0, 1, st);
+  if (W.variant && P.L > 1) {
+    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.ks.done, st);
+    launch_rz(W, L0, 1, st);
+  } else {
+    enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
+    if (P.L == 1) launch_rz(W, L0, 1, st);
+  }
   launch_cg_p(P, W, L0, 0, st);
 }
 
@@ -2006,6 +2051,20 @@ static void pcg_loop(amg_hierarchy* h, Plan& P, Workspace& W, const amg_opts& o,
   }
 }
 
+// smoother | cycle << 1 for the variant cycles (0: the V-cycle with
+// l1-Jacobi); builds the Gauss-Seidel colouring on first use.
+static int check_variant(amg_hierarchy* owner, Plan& P, const amg_opts& o) {
+  AMG_REQUIRE(o.smoother == 0 || o.smoother == 1, "smoother must be 0 (l1-Jacobi) or 1 (Gauss-Seidel)");
+  AMG_REQUIRE(o.cycle == 0 || o.cycle == 1, "cycle must be 0 (V) or 1 (K)");
+  const int variant = o.smoother | (o.cycle << 1);
+  if (!variant || P.L == 1) return 0;
+  AMG_REQUIRE(o.cycle_precision == 64, "the Gauss-Seidel smoother and the K-cycle run with cycle_precision 64");
+  AMG_REQUIRE(owner && &owner->plan == &P && P.nsys == 1,
+              "the Gauss-Seidel smoother and the K-cycle need a single hierarchy (not a batch)");
+  if (o.smoother == 1) ensure_gs(owner, P, owner->own);
+  return variant;
+}
+
 amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_opts& o, cudaStream_t user,
                    amg_info* info) {
   int maxr = 0;
@@ -2014,9 +2073,10 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   AMG_REQUIRE(o.cycle_precision == 64 || o.cycle_precision == 32, "cycle_precision must be 64 or 32");
   AMG_REQUIRE(o.pre >= 1 && o.post >= 1 && o.pre <= 16 && o.post <= 16, "pre and post sweeps must be in [1, 16]");
   AMG_REQUIRE(o.maxit >= 1 && o.rtol >= 0, "maxit must be >= 1 and rtol >= 0");
+  const int variant = check_variant(owner, P, o);
   const int K = round_k(maxr);
   const bool split = o.cycle_precision == 32 && !o.outer_fp64 && P.L > 1;
-  Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, split, o.autotune != 0);
+  Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, split, o.autotune != 0, variant);
   for (KState* v : {&W.ks, &W.ksq, &W.ksf_upd, &W.ksf_post}) {  // the state and its views over other CTA groups
     v->rtol = o.rtol;
     v->maxit = o.maxit;
@@ -2078,8 +2138,9 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
   AMG_REQUIRE(nrhs >= 1 && nrhs <= 32, "nrhs must be in [1, 32]");
   AMG_REQUIRE(o.cycle_precision == 64 || o.cycle_precision == 32, "cycle_precision must be 64 or 32");
   AMG_REQUIRE(o.pre >= 1 && o.post >= 1, "pre and post sweeps must be >= 1");
+  const int variant = check_variant(owner, P, o);
   const int K = round_k(nrhs);
-  Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post);
+  Workspace& W = get_ws(P, K, o.cycle_precision, o.pre, o.post, false, false, variant);
   StreamJoin sj(owner, user);
   cudaStream_t st = owner->own;
   SolveReq rq;
@@ -2096,6 +2157,8 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
   ks.done = W.zero_flag;
   if (P.L == 1) {
     launch_coarse<double>(K, P.co, W.r, W.z, W.zero_flag, st);
+  } else if (W.variant) {
+    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.zero_flag, st);
   } else if (o.cycle_precision == 64) {
     launch_presmooth0<double>(K, P.lev[0], W.rp[0], W.r, static_cast<double*>(W.u[0]), nullptr, W.zero_flag, st);
     enqueue_cycle<double>(nullptr, P, W, st, 2, W.zero_flag, ks, nullptr);

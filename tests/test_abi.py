@@ -4,6 +4,7 @@ import os
 import re
 
 import pytest
+from ctypes import sizeof as C_sizeof
 
 from paper_1907_04417_gb300 import amg, build
 
@@ -35,6 +36,9 @@ def test_default_options_and_struct_layout(lib):
     assert o.tol_svd == 0.1 and o.pre == 1 and o.post == 1 and o.cycle_precision == 64
     assert o.rtol == 1e-8 and o.maxit == 1000
     assert amg.amg_opts.rtol.offset == 24 and amg.amg_info.relres.offset == 16
+    # the variant switches default to the l1-Jacobi V-cycle
+    assert o.smoother == amg.SMOOTHER_L1JACOBI and o.cycle == amg.CYCLE_V
+    assert amg.amg_opts.cycle.offset == 56 and C_sizeof(amg.amg_opts) == 64
 
 
 def test_null_arguments_rejected_without_gpu(lib):
@@ -43,6 +47,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert "non-null" in amg.last_error()
     assert lib.amg_setup_from_aggregates(None, 0, None, None, None, 1, None, None, None) == amg.AMG_ERR_INVALID_ARG
     assert lib.amg_hierarchy_info(None, None) == amg.AMG_ERR_INVALID_ARG
+    assert lib.amg_level_colours(None, 0, None, None) == amg.AMG_ERR_INVALID_ARG
     out = ctypes.c_void_p()
     assert lib.amg_setup_from_aggregates(None, 0, None, None, None, 1, None, None, ctypes.byref(out)) != amg.AMG_OK
 
