@@ -72,6 +72,9 @@ def parse():
                     help="file of tuned launch choices: read when it has this workload, else written "
                          "(so that a profiled run replays the choices of a plain run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", action="store_true",
+                    help="also time the float64 cycle variants (Gauss-Seidel smoother, K-cycle) on the "
+                         "same block, with the level-0 Gauss-Seidel sweep's roofline and an oracle sample")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--profile-kernels", action="store_true",
                     help="also time every kernel family once (eager launches)")
@@ -226,6 +229,7 @@ def algorithmic_bytes(kernel, lv, K, wc):
 
 
 KERNEL_IDS = {"spmv_cg": 1, "restrict_l0": 2, "smooth_l0": 3, "prolong_l0": 4, "cg_update": 5}
+KERNEL_GS_L0 = 6
 
 # q = A p in double-float is bound by float32 arithmetic: per stored non-zero
 # and column the multiply-accumulate of a float pair by a float32 takes 11
@@ -242,6 +246,77 @@ def alu_ops(kernel, lv, K):
     if kernel == "spmv_cg":
         return lv["nnz0"] * K * ALU_OPS_PER_NZ_COL + lv["n0"] * K * ALU_OPS_PER_ROW_COL
     return None
+
+
+def gs_sweep_bytes(lv, K):
+    """Minimal bytes of one level-0 Gauss-Seidel sweep over all colours:
+    the matrix once (8-byte values, 4-byte columns, row pointers), colour and
+    diagonal once per row, f read, u read and written once (float64)."""
+    n0, nnz0 = lv["n0"], lv["nnz0"]
+    return nnz0 * 12 + 4 * (n0 + 1) + n0 * 12 + 3 * n0 * K * 8
+
+
+VARIANTS = [("l1jacobi", "V"), ("gs", "V"), ("l1jacobi", "K"), ("gs", "K")]
+
+
+def time_variants(amg, Hd, Bd, Xd, B, A, lv, K, maxit, peak, stream):
+    """Float64 solves of the block with each cycle variant: device time per
+    RHS (CUDA events on the launching stream, after a warm-up solve that
+    builds the colouring, workspace and graph), iteration counts, true
+    residuals, and for Gauss-Seidel the level-0 sweep's achieved bandwidth."""
+    import numpy as np
+    import torch
+    out = {}
+    for sm, kind in VARIANTS:
+        o = amg.opts(cycle_precision=64, maxit=maxit, smoother=1 if sm == "gs" else 0,
+                     cycle=1 if kind == "K" else 0)
+        Xd.zero_()
+        Hd.solve(Bd, Xd, o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Xd.zero_()
+        e0.record(stream)
+        _, infos, st = Hd.solve(Bd, Xd, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        Xc = Xd.cpu().numpy()
+        rel = float(max(np.linalg.norm(B[:, c] - A @ Xc[:, c]) / np.linalg.norm(B[:, c]) for c in range(K)))
+        its = [i["iters"] for i in infos]
+        ent = {"ms_per_rhs": ms / K, "iters_min": int(min(its)), "iters_max": int(max(its)),
+               "true_relres_max": rel, "status": int(st)}
+        if sm == "gs":
+            Hd.timer_enable(KERNEL_GS_L0)
+            Xd.zero_()
+            Hd.solve(Bd, Xd, o)
+            kms, kn = Hd.timer_read()
+            Hd.timer_enable(0, False)
+            nb = gs_sweep_bytes(lv, K)
+            avg = kms / max(kn, 1)
+            gbs = nb / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+            ent["gs_sweep_l0"] = {"avg_ms": avg, "sweeps": kn, "algorithmic_bytes": nb, "achieved_gbs": gbs,
+                                  "peak_gbs": peak, "frac": gbs / peak, "ncolours": Hd.level_colours(0)[1]}
+        out[f"{sm}/{kind}"] = ent
+    return out
+
+
+def oracle_variant_sample(P, W, smoother, kind, iters_needed, budget_s):
+    """The oracle's PCG with a cycle variant, timed for about ``budget_s``
+    seconds on the same workload and scaled to ``iters_needed``."""
+    from oracle import amg_oracle as O
+    H = O.setup(P.A, P.aggs, P.n_nodes, W)
+    b = P.B[:, 0]
+    pc = lambda r: O.cycle(H, r, smoother=smoother, kind=kind)  # noqa: E731
+    if smoother == "gs":
+        O.gs_data(H)  # the colouring is setup, not timed
+    t0 = time.perf_counter()
+    O.pcg(P.A, b, pc, fixed_iters=1)
+    t1 = time.perf_counter() - t0
+    k = max(2, int(budget_s / max(t1, 1e-3)))
+    t0 = time.perf_counter()
+    O.pcg(P.A, b, pc, fixed_iters=k)
+    dt = time.perf_counter() - t0
+    return {"ms_per_rhs": dt / k * iters_needed * 1e3, "sample_iters": k, "sample_s": dt, "cores": 1}
 
 
 # ------------------------------------------------------------ CPU legs --
@@ -488,6 +563,14 @@ def main():
             "input_gen_s": t_gen, "bootstrap": boot}
     if shares is not None:
         line["kernel_ms_per_solve"] = shares
+    if args.variants:
+        var = time_variants(amg, Hd, Bd, Xd, B, A, lv, args.batch, args.maxit, peak, stream)
+        if rank == 0 and not args.no_cpu_baseline and ws == 1:
+            s = oracle_variant_sample(P, W_recipe, "gs", "K", var["gs/K"]["iters_max"], args.cpu_sample_s)
+            var["gs/K"]["cpu_baseline"] = dict(s, kind="oracle", sample=f"{s['sample_iters']} oracle PCG "
+                                                   f"iterations with the GS K-cycle (setup untimed), scaled "
+                                                   f"to the GPU's {var['gs/K']['iters_max']} iterations")
+        line["variants"] = var
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         s = oracle_sample(P, W_recipe, inf64[0]["iters"], args.cpu_sample_s)
         line["cpu_baseline"] = {"value": s["ms_per_rhs"], "unit": UNIT, "cores": 1, "kind": "oracle",

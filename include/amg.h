@@ -283,7 +283,9 @@ enum {
   AMG_KERNEL_RESTRICT_L0 = 2,    /* fused residual + P^T        (level 0)          */
   AMG_KERNEL_SMOOTH_L0 = 3,      /* post-smoothing with r.z     (level 0)          */
   AMG_KERNEL_PROLONG_L0 = 4,     /* x += P e                    (level 0)          */
-  AMG_KERNEL_CG_UPDATE = 5       /* x, r update with ||r||      (level 0)          */
+  AMG_KERNEL_CG_UPDATE = 5,      /* x, r update with ||r||      (level 0)          */
+  AMG_KERNEL_GS_L0 = 6           /* one backward Gauss-Seidel sweep, all colours
+                                    (level 0, smoother 1; the last post-sweep)      */
 };
 amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
 amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);

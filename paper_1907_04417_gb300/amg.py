@@ -32,6 +32,7 @@ KERNEL_RESTRICT_L0 = 2
 KERNEL_SMOOTH_L0 = 3
 KERNEL_PROLONG_L0 = 4
 KERNEL_CG_UPDATE = 5
+KERNEL_GS_L0 = 6
 
 
 class AMGError(RuntimeError):

@@ -251,8 +251,11 @@ struct VarCycle {
 void ensure_gs(amg_hierarchy* h, Plan& P, cudaStream_t st);
 size_t var_level_ctas(int n, const VarCycle& vc);
 // z = B r (level 0, float64) by one variant cycle; u0 is level-0 scratch.
+// h and pool (may be null) time the level-0 Gauss-Seidel sweeps
+// (AMG_KERNEL_GS_L0) when the handle's timer asks for them.
 void enqueue_var_cycle(const Plan& P, const VarCycle& vc, const double* r, double* z, double* u0,
-                       const int* done, cudaStream_t st);
+                       const int* done, cudaStream_t st, amg_hierarchy* h,
+                       std::vector<cudaEvent_t>* pool);
 // colours of level k in the caller's numbering (the oracle's dof order)
 int level_colours(amg_hierarchy* h, int k, int32_t* colour, cudaStream_t st);
 
@@ -264,6 +267,34 @@ void run_bootstrap_test(const std::vector<amg_hierarchy*>& hs, double* x, int nr
 extern thread_local bool g_capturing;
 void add_launches(long long n);
 long long launches_total();
+
+// Brackets the launches of one kernel family with CUDA events on their
+// stream while the handle's timer asks for that family; the pairs go to
+// ``pool`` and are read back after the solve.
+struct TimedLaunch {
+  amg_hierarchy* h;
+  int id;
+  cudaStream_t st;
+  std::vector<cudaEvent_t>* pool;
+  bool on;
+  cudaEvent_t e1 = nullptr;
+  TimedLaunch(amg_hierarchy* h_, int id_, cudaStream_t st_, std::vector<cudaEvent_t>* pool_)
+      : h(h_), id(id_), st(st_), pool(pool_) {
+    on = h && pool && h->timer.on && h->timer.kernel == id;
+    if (on) {
+      cudaEvent_t e0;
+      AMG_CUDA(cudaEventCreate(&e0));
+      AMG_CUDA(cudaEventCreate(&e1));
+      pool->push_back(e0);
+      pool->push_back(e1);
+      // External records become event-record nodes when the stream is captured
+      AMG_CUDA(cudaEventRecordWithFlags(e0, st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
+    }
+  }
+  ~TimedLaunch() {
+    if (on) cudaEventRecordWithFlags(e1, st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  }
+};
 
 // pointer helpers
 bool is_device_ptr(const void* p);

@@ -1660,30 +1660,7 @@ static void make_var(Plan& P, Workspace& W, int variant) {
 }
 
 // ------------------------------------------------------------- timing --
-struct TimedLaunch {
-  amg_hierarchy* h;
-  int id;
-  cudaStream_t st;
-  std::vector<cudaEvent_t>* pool;
-  bool on;
-  cudaEvent_t e1 = nullptr;
-  TimedLaunch(amg_hierarchy* h_, int id_, cudaStream_t st_, std::vector<cudaEvent_t>* pool_)
-      : h(h_), id(id_), st(st_), pool(pool_) {
-    on = h && pool && h->timer.on && h->timer.kernel == id;
-    if (on) {
-      cudaEvent_t e0;
-      AMG_CUDA(cudaEventCreate(&e0));
-      AMG_CUDA(cudaEventCreate(&e1));
-      pool->push_back(e0);
-      pool->push_back(e1);
-      // External records become event-record nodes when the stream is captured
-      AMG_CUDA(cudaEventRecordWithFlags(e0, st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault));
-    }
-  }
-  ~TimedLaunch() {
-    if (on) cudaEventRecordWithFlags(e1, st, g_capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
-  }
-};
+// TimedLaunch: amg_internal.cuh
 
 // Adds the device time of the first ``keep`` event pairs of ``pool`` (all
 // pairs when keep < 0) to the handle's timer.
@@ -1873,7 +1850,7 @@ static void enqueue_start(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     enqueue_cycle<TC>(h, P, W, st, 0, W.ks.done, W.ks, nullptr);
     launch_rz(W, L0, 0, st);
   } else if (W.variant) {
-    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.ks.done, st);
+    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.ks.done, st, h, nullptr);
     launch_rz(W, L0, 0, st);
   } else {
     if (W.split) {
@@ -1905,7 +1882,7 @@ static void enqueue_iteration(amg_hierarchy* h, Plan& P, Workspace& W, cudaStrea
     else launch_update<TC>(W.K, L0, W.rp[0], W.x, W.r, W.p, W.q, u0, f0, W.ks, st);
   }
   if (W.variant && P.L > 1) {
-    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.ks.done, st);
+    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.ks.done, st, h, pool);
     launch_rz(W, L0, 1, st);
   } else {
     enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
@@ -2158,7 +2135,7 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
   if (P.L == 1) {
     launch_coarse<double>(K, P.co, W.r, W.z, W.zero_flag, st);
   } else if (W.variant) {
-    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.zero_flag, st);
+    enqueue_var_cycle(P, W.var, W.r, W.z, static_cast<double*>(W.u[0]), W.zero_flag, st, nullptr, nullptr);
   } else if (o.cycle_precision == 64) {
     launch_presmooth0<double>(K, P.lev[0], W.rp[0], W.r, static_cast<double*>(W.u[0]), nullptr, W.zero_flag, st);
     enqueue_cycle<double>(nullptr, P, W, st, 2, W.zero_flag, ks, nullptr);

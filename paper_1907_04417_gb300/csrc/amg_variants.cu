@@ -267,7 +267,8 @@ void gs_sweep(const Plan& P, int k, int K, const double* f, double* u, bool back
 }
 
 void level_cycle(const Plan& P, const VarCycle& vc, int k, const double* f, double* out, double* tmp,
-                 const int* done, cudaStream_t st);
+                 const int* done, cudaStream_t st, amg_hierarchy* h = nullptr,
+                 std::vector<cudaEvent_t>* pool = nullptr);
 
 // Two flexible-CG iterations on A_j e = f_j from e = 0, each preconditioned
 // by one cycle on level j; e goes to vc.e[j].
@@ -297,8 +298,10 @@ void fcg2(const Plan& P, const VarCycle& vc, int j, const int* done, cudaStream_
 
 // One cycle on level k for right-hand side f; the result lands in ``out``
 // (``tmp`` is the level's second buffer of the out-of-place Jacobi sweeps).
+// With h and pool, the last backward Gauss-Seidel sweep (one per cycle) is
+// timed as AMG_KERNEL_GS_L0.
 void level_cycle(const Plan& P, const VarCycle& vc, int k, const double* f, double* out, double* tmp,
-                 const int* done, cudaStream_t st) {
+                 const int* done, cudaStream_t st, amg_hierarchy* h, std::vector<cudaEvent_t>* pool) {
   const int K = vc.K;
   if (k == P.L - 1) {
     launch_coarse<double>(K, P.co, f, out, done, st);
@@ -333,6 +336,7 @@ void level_cycle(const Plan& P, const VarCycle& vc, int k, const double* f, doub
   launch_prolong<double>(K, P.tr[k], vc.tp[k], ec, a, done, st);
   for (int s = 0; s < vc.post; ++s) {
     if (vc.smoother == 1) {
+      TimedLaunch tl(s + 1 == vc.post ? h : nullptr, AMG_KERNEL_GS_L0, st, pool);
       gs_sweep(P, k, K, f, a, true, done, st);
     } else {
       launch_smooth<double>(K, vc.nzl[k], L, vc.rp[k], f, a, b, done, st);
@@ -401,10 +405,10 @@ void ensure_gs(amg_hierarchy* h, Plan& P, cudaStream_t st) {
 size_t var_level_ctas(int n, const VarCycle& vc) { return (size_t)((n + vc.dot_rows - 1) / vc.dot_rows); }
 
 void enqueue_var_cycle(const Plan& P, const VarCycle& vc, const double* r, double* z, double* u0, const int* done,
-                       cudaStream_t st) {
+                       cudaStream_t st, amg_hierarchy* h, std::vector<cudaEvent_t>* pool) {
   AMG_REQUIRE(vc.smoother == 0 || P.gs_done, "internal: Gauss-Seidel data missing");
   AMG_REQUIRE(vc.f.size() == (size_t)P.L && vc.f[0] == r, "internal: variant workspace mismatch");
-  level_cycle(P, vc, 0, r, z, u0, done, st);
+  level_cycle(P, vc, 0, r, z, u0, done, st, h, pool);
 }
 
 int level_colours(amg_hierarchy* h, int k, int32_t* colour, cudaStream_t st) {
