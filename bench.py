@@ -191,11 +191,16 @@ def peaks():
 
 
 def kernel_source_hash():
-    """Hash of the sources that define the level-0 solve kernels (their
-    device code and launch choices); stored traffic counts only for them."""
+    """Hash of the device code of the level-0 solve kernels: the shared
+    kernel header, the launchers, and the kernels at the head of
+    amg_solve.cu (everything before its host-side workspace).  Stored
+    traffic counts only while this hash is unchanged."""
     h = hashlib.sha256()
-    for f in ("amg_kernels.cuh", "amg_solve.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1907_04417_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_1907_04417_gb300", "csrc")
+    for f in ("amg_kernels.cuh", "amg_launch.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    src = open(os.path.join(csrc, "amg_solve.cu"), "rb").read()
+    h.update(src[:src.index(b"struct Workspace {")])
     return h.hexdigest()[:16]
 
 
