@@ -175,6 +175,8 @@ struct Plan {
   std::vector<int*> gs_colour;
   std::vector<double*> gs_diag;
   std::vector<int> gs_ncol;
+  std::vector<int*> gs_rows;                 // rows sorted by colour, ascending within a colour
+  std::vector<std::vector<int>> gs_cstart;   // ncol + 1 offsets into gs_rows
   Plan() : arena(new Arena) {}
   ~Plan();
 };

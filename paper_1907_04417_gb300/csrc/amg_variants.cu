@@ -6,9 +6,9 @@
 //    is two flexible-CG iterations preconditioned by the cycle one level
 //    down (a nonlinear AMLI cycle).
 // Restriction, prolongation, the l1-Jacobi sweeps and the coarsest solve are
-// the V-cycle's own launchers; this file adds the colouring, the colour
-// sweeps, the level SpMV, the column inner products and the flexible-CG
-// updates.
+// the V-cycle's own launchers; this file adds the colouring (and the rows of
+// every colour, listed once at setup), the colour sweeps, the level SpMV, the
+// column inner products and the flexible-CG updates.
 #include <algorithm>
 #include <vector>
 
@@ -94,20 +94,21 @@ __global__ void k_diag(int n, const int* __restrict__ rowptr, const int* __restr
   diag[i] = d;
 }
 
-// Rows of colour c: u_i <- u_i + (f_i - (A u)_i) / a_ii, one thread per
-// (row, column); the K threads of a row touch K contiguous values.
-__global__ void k_gs_colour(int n, int K, int c, const int* __restrict__ colour, const int* __restrict__ rowptr,
-                            const int* __restrict__ col, const double* __restrict__ val,
-                            const double* __restrict__ diag, const double* __restrict__ f, double* u,
-                            const int* __restrict__ done) {
+// The rows of one colour (listed in ``rows``, ascending):
+// u_i <- u_i + (f_i - (A u)_i) / a_ii, one thread per (listed row, column);
+// the K threads of a row touch K contiguous values.
+__global__ void k_gs_rows(int cnt, int K, const int* __restrict__ rows, const int* __restrict__ rowptr,
+                          const int* __restrict__ col, const double* __restrict__ val,
+                          const double* __restrict__ diag, const double* __restrict__ f, double* u,
+                          const int* __restrict__ done) {
   if (*done) return;
   const long long t = (long long)blockIdx.x * VB + threadIdx.x;
-  if (t >= (long long)n * K) return;
-  const int i = (int)(t / K), q = (int)(t % K);
-  if (colour[i] != c) return;
-  double s = f[t];
+  if (t >= (long long)cnt * K) return;
+  const int i = rows[t / K], q = (int)(t % K);
+  const size_t e = (size_t)i * K + q;
+  double s = f[e];
   for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) s -= val[j] * u[(size_t)col[j] * K + q];
-  u[t] = u[t] + s / diag[i];
+  u[e] = u[e] + s / diag[i];
 }
 
 // u = D^{-1} f (the first l1-Jacobi sweep from zero)
@@ -258,10 +259,13 @@ void gs_sweep(const Plan& P, int k, int K, const double* f, double* u, bool back
               cudaStream_t st) {
   const Level& L = P.lev[k];
   const int nc = P.gs_ncol[k];
+  const std::vector<int>& cs = P.gs_cstart[k];
   for (int q = 0; q < nc; ++q) {
     const int c = backward ? nc - 1 - q : q;
-    k_gs_colour<<<grid_of((long long)L.n * K), VB, 0, st>>>(L.n, K, c, P.gs_colour[k], L.rowptr, L.col, L.val64,
-                                                            P.gs_diag[k], f, u, done);
+    const int cnt = cs[c + 1] - cs[c];
+    if (cnt == 0) continue;
+    k_gs_rows<<<grid_of((long long)cnt * K), VB, 0, st>>>(cnt, K, P.gs_rows[k] + cs[c], L.rowptr, L.col, L.val64,
+                                                          P.gs_diag[k], f, u, done);
     AMG_LAUNCH_CHECK();
   }
 }
@@ -354,6 +358,8 @@ void ensure_gs(amg_hierarchy* h, Plan& P, cudaStream_t st) {
   P.gs_colour.assign(ns, nullptr);
   P.gs_diag.assign(ns, nullptr);
   P.gs_ncol.assign(ns, 0);
+  P.gs_rows.assign(ns, nullptr);
+  P.gs_cstart.assign(ns, {});
   Arena tmp;
   int* flag = tmp.alloc<int>(2);
   int* h_flag = nullptr;
@@ -389,10 +395,24 @@ void ensure_gs(amg_hierarchy* h, Plan& P, cudaStream_t st) {
       AMG_CUDA(cudaStreamSynchronize(st));
       AMG_REQUIRE(h_flag[1] == 0, "Gauss-Seidel needs a positive diagonal on every smoothed level");
       int mx = -1;
-      for (int c : hc) mx = std::max(mx, c);
+      for (int c : hc) {
+        AMG_REQUIRE(c >= 0, "internal: a row was left uncoloured");
+        mx = std::max(mx, c);
+      }
+      // rows grouped by colour (a counting sort: ascending rows within a colour)
+      std::vector<int> cs(mx + 2, 0), rows(n);
+      for (int c : hc) cs[c + 1]++;
+      for (int c = 0; c <= mx; ++c) cs[c + 1] += cs[c];
+      std::vector<int> pos(cs.begin(), cs.end() - 1);
+      for (int i = 0; i < n; ++i) rows[pos[hc[i]]++] = i;
+      int* d_rows = P.arena->alloc<int>(n);
+      AMG_CUDA(cudaMemcpyAsync(d_rows, rows.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st));
+      AMG_CUDA(cudaStreamSynchronize(st));
       P.gs_colour[k] = colour;
       P.gs_diag[k] = diag;
       P.gs_ncol[k] = mx + 1;
+      P.gs_rows[k] = d_rows;
+      P.gs_cstart[k] = cs;
     }
   } catch (...) {
     cudaFreeHost(h_flag);
