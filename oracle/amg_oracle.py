@@ -277,18 +277,24 @@ def coarsening_ratio(H: Hierarchy) -> float:
 # bootstrap (Algorithm 1, Section 2): the testing phase and the driver
 # --------------------------------------------------------------------------
 
-def composite_error(Hs, A, x, symmetric: bool = True):
+def composite_error(Hs, A, x, symmetric: bool = True, smoother: str = "l1jacobi", kind: str = "V"):
     """One application of the composite error operator of Algorithm 1 to x
-    (vector or n x K).  With hierarchies H_1..H_r (B_k one V-cycle of H_k)
-    the plain product is E = (I - B_r A) ... (I - B_1 A), Eq. (comp_AMG):
-    the rightmost factor acts first.  The symmetrized product of Section 5
-    (i) is (I - B_1 A) ... (I - B_r A) (I - B_r A) ... (I - B_1 A): factors
+    (vector or n x K).  With hierarchies H_1..H_r (B_k one cycle of H_k:
+    the V-cycle with l1-Jacobi by default, or the ``cycle`` variant that
+    smoother and kind select, e.g. the paper's Gauss-Seidel K-cycles) the
+    plain product is E = (I - B_r A) ... (I - B_1 A), Eq. (comp_AMG): the
+    rightmost factor acts first.  The symmetrized product of Section 5 (i)
+    is (I - B_1 A) ... (I - B_r A) (I - B_r A) ... (I - B_1 A): factors
     1, 2, ..., r, then r, ..., 2, 1."""
     order = list(range(len(Hs)))
     seq = order + order[::-1] if symmetric else order
     v = np.array(x, dtype=np.float64)
     for k in seq:
-        v = v - vcycle(Hs[k], A @ v)
+        g = A @ v
+        if smoother == "l1jacobi" and kind == "V":
+            v = v - vcycle(Hs[k], g)
+        else:
+            v = v - cycle(Hs[k], g, smoother=smoother, kind=kind)
     return v
 
 
@@ -299,7 +305,7 @@ def a_norm(A, x):
     return np.sqrt(np.einsum("ij,ij->j", X2, A @ X2))
 
 
-def bootstrap_test(Hs, A, x0, nu: int, symmetric: bool = True):
+def bootstrap_test(Hs, A, x0, nu: int, symmetric: bool = True, smoother: str = "l1jacobi", kind: str = "V"):
     """Testing phase of Algorithm 1: x^j = E x^{j-1}, j = 1..nu, from x^0 =
     x0.  Returns (x^nu, rho) with the convergence estimate rho =
     (||x^nu||_A / ||x^0||_A)^(1/nu) per column (the paper leaves the estimate
@@ -307,14 +313,15 @@ def bootstrap_test(Hs, A, x0, nu: int, symmetric: bool = True):
     x = np.array(x0, dtype=np.float64)
     n0 = a_norm(A, x)
     for _ in range(nu):
-        x = composite_error(Hs, A, x, symmetric)
+        x = composite_error(Hs, A, x, symmetric, smoother, kind)
     n1 = a_norm(A, x)
     with np.errstate(divide="ignore", invalid="ignore"):
         rho = np.where(n0 > 0, (n1 / n0) ** (1.0 / nu), 0.0)
     return x, rho
 
 
-def bootstrap(A, w0, m: int, nu: int, aggregate, starts, symmetric: bool = True, tol: float = 0.1):
+def bootstrap(A, w0, m: int, nu: int, aggregate, starts, symmetric: bool = True, tol: float = 0.1,
+              smoother: str = "l1jacobi", kind: str = "V"):
     """Algorithm 1 with maxstage = m - 1 and rho_des = 0 (the number of
     smooth vectors is fixed instead of the target rate).  Stage r = 1..m-1
     builds B_r from w_{r-1}: ``aggregate(w)`` gives the composed pairwise
@@ -331,7 +338,7 @@ def bootstrap(A, w0, m: int, nu: int, aggregate, starts, symmetric: bool = True,
         w = W[:, r - 1]
         aggs, n_nodes = aggregate(w)
         Hs.append(setup(A, aggs, n_nodes, (w / np.linalg.norm(w))[:, None], tol))
-        x, rho = bootstrap_test(Hs, A, starts[r - 1], nu, symmetric)
+        x, rho = bootstrap_test(Hs, A, starts[r - 1], nu, symmetric, smoother, kind)
         W[:, r] = x / a_norm(A, x)[0]
         rhos.append(float(rho[0]))
     return W, rhos

@@ -346,12 +346,14 @@ def test_bootstrap_composite_matches_dense_product():
     assert np.abs(E1 @ E2 @ x - E2 @ E1 @ x).max() > 1e-6
 
 
-def test_bootstrap_symmetric_product_is_a_selfadjoint_contraction():
-    """With SPD V-cycles each I - B_k A is A-self-adjoint with A-norm < 1, so
-    the symmetrized product is A-self-adjoint with spectrum in [0, 1)."""
+@pytest.mark.parametrize("smoother", ["l1jacobi", "gs"])
+def test_bootstrap_symmetric_product_is_a_selfadjoint_contraction(smoother):
+    """With SPD V-cycles (l1-Jacobi, or forward/backward Gauss-Seidel) each
+    I - B_k A is A-self-adjoint with A-norm < 1, so the symmetrized product
+    is A-self-adjoint with spectrum in [0, 1)."""
     A, Hs = _bootstrap_hierarchies()
     n = A.shape[0]
-    E = np.stack([O.composite_error(Hs, A, e, symmetric=True) for e in np.eye(n)], axis=1)
+    E = np.stack([O.composite_error(Hs, A, e, symmetric=True, smoother=smoother) for e in np.eye(n)], axis=1)
     AE = A.toarray() @ E
     np.testing.assert_allclose(AE, AE.T, atol=1e-12 * np.abs(AE).max())
     lam = sla.eigh(AE, A.toarray(), eigvals_only=True)
@@ -372,6 +374,21 @@ def test_bootstrap_rho_tends_to_the_largest_eigenvalue():
     assert rho100[0] <= lam_max * (1 + 1e-12)  # no A-norm reduction factor exceeds the spectral radius
     _, rho1 = O.bootstrap_test(Hs, A, x0, nu=1, symmetric=True)
     np.testing.assert_allclose(rho1[0], O.a_norm(A, E @ x0)[0] / O.a_norm(A, x0)[0], rtol=1e-12)
+
+
+def test_bootstrap_kcycle_composite_is_homogeneous_and_contracts():
+    """With the paper's Gauss-Seidel K-cycles the composite operator is no
+    longer linear, but it stays positively homogeneous, and on these stages
+    it reduces the A-norm (the K-cycle approximates A^{-1} better than the
+    V-cycle: its reduction is the smaller)."""
+    A, Hs = _bootstrap_hierarchies(16)
+    x = np.random.default_rng(9).standard_normal(A.shape[0])
+    Ek = O.composite_error(Hs, A, x, smoother="gs", kind="K")
+    np.testing.assert_allclose(O.composite_error(Hs, A, 2.5 * x, smoother="gs", kind="K"), 2.5 * Ek, rtol=1e-12)
+    Ev = O.composite_error(Hs, A, x, smoother="gs", kind="V")
+    assert O.a_norm(A, Ek)[0] < O.a_norm(A, Ev)[0] < O.a_norm(A, x)[0]
+    _, rho = O.bootstrap_test(Hs, A, x, nu=3, smoother="gs", kind="K")
+    assert 0.0 < rho[0] < 1.0
 
 
 def test_bootstrap_one_level_stage_annihilates():
