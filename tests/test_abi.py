@@ -60,3 +60,37 @@ def test_bootstrap_test_rejects_bad_arguments_without_gpu(lib):
     x = (ctypes.c_double * 4)()
     assert lib.amg_bootstrap_test(hp, 1, x, 1, 1, 1, None, None, None, None) == amg.AMG_ERR_INVALID_ARG
     assert "hierarchy" in amg.last_error()
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """include/amg.h compiles as strict C99, and a C program links against
+    the library and calls the entry points that need no GPU."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fsyntax-only", "-x", "c",
+                        os.path.join(inc, "amg.h")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    src = tmp_path / "use_amg.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "amg.h"\n'
+        "int main(void) {\n"
+        "  amg_opts o; amg_hier_info hi; int32_t nc = 0;\n"
+        "  amg_default_opts(&o);\n"
+        "  amg_status s1 = amg_hierarchy_info(NULL, &hi);\n"
+        "  amg_status s2 = amg_level_colours(NULL, 0, NULL, &nc);\n"
+        '  printf("%d %d %d %d %d %d %s\\n", o.pre, o.post, o.cycle_precision, o.smoother, o.cycle,\n'
+        "         (int)(s1 == AMG_ERR_INVALID_ARG && s2 == AMG_ERR_INVALID_ARG), amg_last_error());\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "use_amg"
+    libdir = os.path.dirname(amg.LIB_PATH)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", str(src), "-I", inc, "-L", libdir, "-lamg_gb300",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    fields = r.stdout.split()
+    assert fields[:6] == ["1", "1", "64", "0", "0", "1"], r.stdout
