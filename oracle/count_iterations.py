@@ -5,10 +5,13 @@ generators) and writes tests/golden/oracle_iterations.json.  The benchmark's
 CPU legs time a bounded number of oracle iterations and scale the per-
 iteration time by these counts.
 
-    python oracle/count_iterations.py [--bootstrap] [grid ...]
+    python oracle/count_iterations.py [--bootstrap] [--variant=SMOOTHER/KIND] [grid ...]
 
 With --bootstrap the smooth vectors come from the oracle's own bootstrap
 (Algorithm 1) on the seeded starts instead of the relaxed-vector recipe.
+With --variant (gs/V, l1jacobi/K or gs/K) the preconditioner is that cycle
+variant (Section 5: Gauss-Seidel smoothing, K-cycles) instead of the
+l1-Jacobi V-cycle; the key gains the suffix _<smoother><kind>.
 """
 import json
 import os
@@ -38,12 +41,15 @@ def bootstrap_vectors(P, N):
     return W / np.linalg.norm(W, axis=0), rhos
 
 
-def main(grids, bootstrap=False):
+def main(grids, bootstrap=False, variant=None):
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    smoother, kind = variant.split("/") if variant else ("l1jacobi", "V")
     for N in grids:
         P = inputs.anisotropic(N=N, nrhs=1)
-        key = f"aniso9_{N}x{N}" + ("_bootstrap" if bootstrap else "")
+        key = f"aniso9_{N}x{N}" + ("_bootstrap" if bootstrap else "") + (f"_{smoother}{kind}" if variant else "")
         note = "FP64 oracle, zero initial guess, RHS seed 1002 uniform[-1,1]"
+        if variant:
+            note += f"; cycle variant: smoother {smoother}, {kind}-cycle"
         if bootstrap:
             t0 = time.time()
             P.W, rhos = bootstrap_vectors(P, N)
@@ -52,7 +58,10 @@ def main(grids, bootstrap=False):
         H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
         ts = time.time() - t0
         t0 = time.time()
-        x, res = O.solve(H, P.B[:, 0], maxit=5000)
+        if variant:
+            x, res = O.solve_variant(H, P.B[:, 0], maxit=5000, smoother=smoother, kind=kind)
+        else:
+            x, res = O.solve(H, P.B[:, 0], maxit=5000)
         tsol = time.time() - t0
         b = P.B[:, 0]
         data[key] = {
@@ -68,4 +77,5 @@ def main(grids, bootstrap=False):
 
 if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    main([int(a) for a in args] or [1024], bootstrap="--bootstrap" in sys.argv)
+    var = next((a.split("=", 1)[1] for a in sys.argv[1:] if a.startswith("--variant=")), None)
+    main([int(a) for a in args] or [1024], bootstrap="--bootstrap" in sys.argv, variant=var)
