@@ -375,37 +375,29 @@ def priority_rank(n: int) -> np.ndarray:
 
 
 def greedy_colouring(A: sp.csr_matrix) -> np.ndarray:
-    """Greedy colouring of the graph of A (its stored off-diagonal pattern)
-    in decreasing priority order: every vertex takes the smallest colour that
-    none of its higher-priority neighbours holds.  Computed in rounds: a
-    vertex is coloured in the round in which all its higher-priority
-    neighbours are coloured, which gives the same colours as visiting the
-    vertices one by one in priority order (a vertex's colour depends only on
-    its higher-priority neighbours)."""
+    """Greedy colouring of the graph of A (its stored off-diagonal pattern),
+    one vertex at a time in decreasing priority (splitmix64(i), i): every
+    vertex takes the smallest colour that none of its already coloured
+    neighbours holds (those are exactly its higher-priority neighbours)."""
     A = sp.csr_matrix(A)
     n = A.shape[0]
-    rows = np.repeat(np.arange(n), np.diff(A.indptr))
-    cols = A.indices
-    off = rows != cols
-    rows, cols = rows[off], cols[off]
     rank = priority_rank(n)
-    higher = rank[cols] > rank[rows]
-    hr, hc = rows[higher], cols[higher]          # edges to higher-priority neighbours
-    deg = np.bincount(hr, minlength=n)
-    colour = np.full(n, -1, dtype=np.int64)
-    while np.any(colour < 0):
-        waiting = np.bincount(hr[colour[hc] < 0], minlength=n)
-        ready = np.flatnonzero((colour < 0) & (waiting == 0))
-        width = int(deg[ready].max(initial=0)) + 2
-        slot = np.full(n, -1, dtype=np.int64)
-        slot[ready] = np.arange(ready.size)
-        used = np.zeros((ready.size, width), dtype=bool)
-        e = slot[hr] >= 0
-        c = colour[hc[e]]
-        keep = c < width
-        used[slot[hr[e]][keep], c[keep]] = True
-        colour[ready] = np.argmin(used, axis=1)
-    return colour
+    order = np.empty(n, dtype=np.int64)
+    order[n - 1 - rank] = np.arange(n)          # order[0] = highest priority
+    indptr = A.indptr.tolist()
+    indices = A.indices.tolist()
+    colour = [-1] * n
+    for v in order.tolist():
+        taken = set()
+        for q in range(indptr[v], indptr[v + 1]):
+            j = indices[q]
+            if j != v and colour[j] >= 0:
+                taken.add(colour[j])
+        c = 0
+        while c in taken:
+            c += 1
+        colour[v] = c
+    return np.asarray(colour, dtype=np.int64)
 
 
 def gs_sweep(A: sp.csr_matrix, diag, colour, f, u, backward: bool = False):
@@ -519,3 +511,120 @@ def solve_variant(H: Hierarchy, b, rtol=1e-8, maxit=1000, fixed_iters=None, pre=
     res = [pcg(A, cols[:, c], pc, rtol, maxit, fixed_iters=fixed_iters) for c in range(cols.shape[1])]
     X = np.stack([r.x for r in res], axis=1)
     return (X[:, 0] if B.ndim == 1 else X), res
+
+
+# --------------------------------------------------------------------------
+# compatible weighted matching (Section 3): one pairwise aggregation step
+# --------------------------------------------------------------------------
+
+def matching_weight(a_ii, a_jj, a_ij, w_i, w_j):
+    """Edge weight of the compatible weighted matching for the edge (i, j):
+    the diagonal entry of A_f = P_f^T A P_f that the D-orthogonal local
+    vector w_e^perp of Eq. (vector w_e) produces, normalised by its D_e-norm,
+        (w_e^perp)^T A_e w_e^perp / (w_e^perp)^T D_e w_e^perp
+            = 1 - 2 a_ij w_i w_j / (a_ii w_i^2 + a_jj w_j^2).
+    Section 3 asks for the matching that maximises the product of these
+    entries.  The right-hand form is evaluated in float64, one rounded
+    operation at a time, left to right: den = a_ii w_i w_i + a_jj w_j w_j,
+    then 1 - (2 a_ij w_i w_j) / den.  A non-positive denominator gives 0
+    (the edge takes no part)."""
+    den = a_ii * w_i * w_i + a_jj * w_j * w_j
+    if not den > 0.0:
+        return 0.0
+    return 1.0 - 2.0 * a_ij * w_i * w_j / den
+
+
+def matching_edges(A: sp.csr_matrix, w):
+    """The edges (i, j), i < j, of the graph of A (its stored upper entries,
+    row by row) with their weights c_ij."""
+    A = sp.csr_matrix(A)
+    diag = A.diagonal()
+    w = [float(v) for v in np.asarray(w, dtype=np.float64)]
+    edges = []
+    for i in range(A.shape[0]):
+        for q in range(A.indptr[i], A.indptr[i + 1]):
+            j = int(A.indices[q])
+            if j > i:
+                c = matching_weight(float(diag[i]), float(diag[j]), float(A.data[q]), w[i], w[j])
+                edges.append((i, j, c))
+    return edges
+
+
+def greedy_matching(n: int, edges):
+    """The matching of one pairwise step: the edges with c_ij > 0 are visited
+    one at a time in the strict order (c_ij descending, then i, then j) and an
+    edge joins the matching when neither end is matched yet.  This greedy
+    matching stands in for the maximum product matching of Section 3 (it is a
+    1/2-approximation of the maximum weight matching).  Returns mate[v], the
+    partner of v or -1."""
+    mate = np.full(n, -1, dtype=np.int64)
+    for i, j, c in sorted((e for e in edges if e[2] > 0.0), key=lambda e: (-e[2], e[0], e[1])):
+        if mate[i] < 0 and mate[j] < 0:
+            mate[i] = j
+            mate[j] = i
+    return mate
+
+
+def pairwise_prolongator(w, mate):
+    """Eq. (prol): the aggregates of one pairwise step and the prolongator
+    P_c with one column per aggregate.  Each pair {i, j} and each unmatched
+    vertex k is an aggregate; the aggregates are numbered by their smallest
+    member, in increasing order (the paper lists pairs before singletons;
+    the numbering does not change the coarse space).  Column values: the
+    local vector w_e = [w_i, w_j] / sqrt(w_i^2 + w_j^2) of Eq. (vector w_e)
+    for a pair, w_k / |w_k| for a singleton (the matrix W of Eq. (prol)).
+    Where the paper's formula divides by zero: a singleton with w_k = 0 takes
+    1, a pair with w_i = w_j = 0 takes equal weights 1/sqrt(2).
+    Returns (agg, P_c) with agg[v] the aggregate of v."""
+    w = np.asarray(w, dtype=np.float64)
+    n = w.size
+    agg = np.full(n, -1, dtype=np.int64)
+    na = 0
+    for v in range(n):                       # smallest member first
+        if agg[v] >= 0:
+            continue
+        agg[v] = na
+        if mate[v] >= 0:
+            agg[mate[v]] = na
+        na += 1
+    vals = np.empty(n)
+    for v in range(n):
+        u = mate[v]
+        if u < 0:
+            vals[v] = -1.0 if w[v] < 0 else 1.0
+        else:
+            nrm = np.sqrt(w[v] * w[v] + w[u] * w[u])
+            vals[v] = w[v] / nrm if nrm > 0 else np.sqrt(0.5)
+    P = sp.csr_matrix((vals, (np.arange(n), agg)), shape=(n, na))
+    return agg, P
+
+
+def pairwise_step(A: sp.csr_matrix, w):
+    """One pairwise aggregation step of Section 3 on (A, w): weights,
+    greedy matching, Eq. (prol), then the next graph A_c = P_c^T A P_c and
+    the next vector w_c = P_c^T w (the coarse level the following step
+    matches on).  Returns (agg, mate, P_c, A_c, w_c)."""
+    A = sp.csr_matrix(A, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    mate = greedy_matching(A.shape[0], matching_edges(A, w))
+    agg, P = pairwise_prolongator(w, mate)
+    Ac = (P.T @ A @ P).tocsr()
+    Ac.sort_indices()
+    return agg, mate, P, Ac, P.T @ w
+
+
+def aggregate_hierarchy(A: sp.csr_matrix, w, steps_per_level):
+    """Aggressive coarsening (end of Section 3): steps_per_level[k]
+    consecutive pairwise steps make the level-(k+1) aggregates of the
+    level-k nodes; the composed map is the product of the pairwise maps.
+    Returns (aggs, n_nodes) in the form ``setup`` takes."""
+    aggs, n_nodes = [], [A.shape[0]]
+    Ak, wk = sp.csr_matrix(A, dtype=np.float64), np.asarray(w, dtype=np.float64)
+    for s in steps_per_level:
+        comp = np.arange(Ak.shape[0])
+        for _ in range(s):
+            agg, _, _, Ak, wk = pairwise_step(Ak, wk)
+            comp = agg[comp]
+        aggs.append(comp.astype(np.int32))
+        n_nodes.append(int(Ak.shape[0]))
+    return aggs, n_nodes

@@ -1,6 +1,7 @@
 """Pins of the oracle's cycle variants (Section 5: forward/backward
 Gauss-Seidel smoothing, K-cycles with two inner flexible-CG iterations)
-against facts that do not re-type the oracle: a sequential greedy colouring,
+against facts that do not re-type the oracle: the colouring computed in
+Jones-Plassmann rounds,
 closed forms on complete graphs, triangular solves of the permuted system,
 Krylov and Galerkin minimisers, symmetry and homogeneity of the
 preconditioners."""
@@ -22,19 +23,30 @@ def _splitmix_int(i):
     return z ^ (z >> 31)
 
 
-def _sequential_greedy(A):
-    """Vertices one at a time in decreasing (splitmix64(i), i) order; each
-    takes the smallest colour absent from its already coloured neighbours."""
+def _jones_plassmann(A):
+    """Colouring in rounds (Jones & Plassmann 1993): in each round every
+    uncoloured vertex whose higher-priority neighbours (larger
+    (splitmix64(i), i)) are all coloured takes the smallest colour none of
+    them holds.  A vertex's colour depends only on its higher-priority
+    neighbours, so this gives the greedy colouring in priority order by
+    another route (it is how the device computes it)."""
     A = sp.csr_matrix(A)
     n = A.shape[0]
-    order = sorted(range(n), key=lambda i: (_splitmix_int(i), i), reverse=True)
+    key = [(_splitmix_int(i), i) for i in range(n)]
+    nbr = [[j for j in A.indices[A.indptr[v]:A.indptr[v + 1]] if j != v] for v in range(n)]
+    higher = [[j for j in nbr[v] if key[j] > key[v]] for v in range(n)]
     colour = [-1] * n
-    for v in order:
-        taken = {colour[j] for j in A.indices[A.indptr[v]:A.indptr[v + 1]] if j != v and colour[j] >= 0}
-        c = 0
-        while c in taken:
-            c += 1
-        colour[v] = c
+    left = set(range(n))
+    while left:
+        ready = [v for v in left if all(colour[j] >= 0 for j in higher[v])]
+        assert ready
+        for v in ready:
+            taken = {colour[j] for j in higher[v]}
+            c = 0
+            while c in taken:
+                c += 1
+            colour[v] = c
+        left -= set(ready)
     return np.asarray(colour)
 
 
@@ -67,7 +79,7 @@ def test_splitmix64_matches_integer_definition():
 
 
 @pytest.mark.parametrize("which", ["poisson12", "aniso16", "coarse", "random"])
-def test_colouring_equals_sequential_greedy(which):
+def test_colouring_equals_jones_plassmann_rounds(which):
     if which == "poisson12":
         A = problems.poisson5(12)
     elif which == "aniso16":
@@ -77,7 +89,7 @@ def test_colouring_equals_sequential_greedy(which):
         A = H.levels[1].A
     else:
         A = _random_graph()
-    np.testing.assert_array_equal(O.greedy_colouring(A), _sequential_greedy(A))
+    np.testing.assert_array_equal(O.greedy_colouring(A), _jones_plassmann(A))
 
 
 def test_colouring_complete_graph_closed_form():
