@@ -66,11 +66,16 @@ typedef struct {
   int32_t use_graph;       /* 1: PCG iterations replayed from a CUDA graph.      1 */
   int32_t check_every;     /* iterations between convergence reads on the host.  8 */
   int32_t autotune;        /* 1: time SpMV lane layouts once per (level, nrhs).  1 */
-  int32_t outer_fp64;      /* float32-cycle mode only.  0: the outer q = A p runs in
-                              double-float arithmetic (hi + lo float pairs with
-                              error-free products and sums, about 2^-44 relative
-                              accuracy) on the float32 pipes; 1: float64 FMAs.
-                              The CG recurrences and dots stay float64 either way. 0 */
+  int32_t outer_fp64;      /* float32-cycle mode only.  1: the outer CG keeps x, r,
+                              p and q in float64 and forms q = A p with float64
+                              FMAs; the cycle takes r rounded to float32.
+                              0: x, r and q are double-float pairs (hi + lo
+                              float32, about 2^-44 relative), the search
+                              direction p is rounded to float32 when it is
+                              formed, and q = A p runs in double-float
+                              arithmetic (error-free products and sums) on the
+                              float32 pipes.  In both modes alpha, beta and the
+                              reduced dot products and norms are float64.     0 */
   int32_t smoother;        /* 0: l1-Jacobi.  1: Gauss-Seidel, forward sweeps before
                               and backward sweeps after the coarse correction
                               (Section 5), rows visited colour by colour in a
@@ -291,17 +296,19 @@ amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
 amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);
 
 /*
- * Local bases of Eq. (svd) computed without any device allocation.  The paper
- * has no counterpart: this entry point exists for callers that may not call
- * cudaMalloc when they run (a real-time or latency-bound loop where an
- * allocation can stall the device, a plug-in whose host framework owns every
- * device allocation, a pipeline held to a pre-reserved memory budget).
+ * Per-aggregate orthonormal bases, as amg_setup_from_aggregates builds them,
+ * computed without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not call cudaMalloc when they
+ * run (a real-time or latency-bound loop where an allocation can stall the
+ * device, a plug-in whose host framework owns every device allocation, a
+ * pipeline held to a pre-reserved memory budget).
  *
  * It runs the per-aggregate computation of amg_setup_from_aggregates on
  * caller-owned device arrays and gives the same bases:
  *  W          nf x m row-major float64, device: the smooth vectors, with the
  *             rows of aggregate a at [row_start[a], row_start[a+1]).
- *  row_start  int32[nagg+1], device, increasing, row_start[nagg] <= nf.
+ *  row_start  int32[nagg+1], device, strictly increasing, row_start[0] >= 0,
+ *             row_start[nagg] <= nf.
  *  nf         rows of the level (size(A) in the truncation threshold).
  *  tol        TOL of the truncation rule.
  *  U          nf x m row-major float64, device, output: rows of aggregate a
@@ -310,11 +317,13 @@ amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);
  * The only extra memory is a work area of AMG_LOCAL_BASES_STATIC_DOUBLES
  * doubles (1 MiB) compiled into the library, held by every GPU that loads it
  * until the process exits; nf * m beyond that size is rejected with
- * AMG_ERR_INVALID_ARG, as are host pointers and invalid row ranges.  Calls on
- * one device share the work area: calls that may overlap on the GPU race and
- * must be ordered by the caller.  The first call on each device looks up the
- * work area's device address; make it before capturing any stream.  The call
- * synchronises ``stream`` before returning.
+ * AMG_ERR_INVALID_ARG, as are host pointers and invalid row ranges, each with
+ * its reason in amg_last_error().  Calls on one device share the work area:
+ * calls that may overlap on the GPU race and must be ordered by the caller.
+ * The first call on each device looks up the work area's device address and
+ * keeps it; make that first call before capturing any stream, and do not
+ * call cudaDeviceReset on that device afterwards (the kept address would be
+ * stale).  The call synchronises ``stream`` before returning.
  */
 #define AMG_LOCAL_BASES_STATIC_DOUBLES (1 << 17)
 amg_status amg_local_bases_static(const double* W, int32_t m, const int32_t* row_start,

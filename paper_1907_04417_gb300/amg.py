@@ -234,6 +234,9 @@ class Hierarchy:
         self.n = n
         self.nnz = int(col.shape[0])
         self.m = m
+        # the matrix values the hierarchy was built from (caller CSR order),
+        # so that a caller can check that a solve still belongs to them
+        self.setup_values = val.detach().clone() if _is_torch(val) else np.array(val, dtype=np.float64)
 
     def close(self):
         if getattr(self, "h", None):

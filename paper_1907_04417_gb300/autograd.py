@@ -6,9 +6,10 @@ preconditioned CG solve with the same hierarchy, A lambda = g (A is SPD, so
 A^{-T} = A^{-1}), followed by the fused kernel that writes
 dL/da_ij = -sum_c lambda[i, c] x[j, c] for every stored entry of A.  The
 gradient with respect to b is lambda.  ``values`` must hold A's CSR values in
-the CSR order the hierarchy was set up with; the hierarchy itself is treated
-as a constant preconditioner (the derivative of the exact solution does not
-depend on it).
+the CSR order the hierarchy was set up with, and equal them: the forward
+solve refuses values that differ from the hierarchy's (a changed matrix needs
+a new Hierarchy).  The hierarchy is a constant preconditioner (the derivative
+of the exact solution does not depend on it).
 
 ``CellCentredDiffusion`` assembles the cell-centred 5-point operator of the
 differentiable workload from a cell coefficient field with torch operations,
@@ -23,9 +24,24 @@ from . import amg
 from .hostsetup import problems
 
 
+def check_values(values, hierarchy):
+    """Refuse a solve whose matrix values differ from those the hierarchy was
+    set up with: the forward solve and the gradient would belong to the old
+    matrix.  A caller that changes A (an optimisation step on the
+    coefficients) builds a new Hierarchy."""
+    ref = hierarchy.setup_values
+    v = values.detach()
+    if isinstance(ref, np.ndarray):
+        ref = torch.from_numpy(ref)
+    if v.shape != ref.shape or not torch.equal(v.to(device=ref.device, dtype=ref.dtype), ref):
+        raise ValueError("values differ from the matrix the hierarchy was set up with; "
+                         "build a new Hierarchy for the new matrix")
+
+
 class AMGSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, values, b, hierarchy, options=None):
+        check_values(values, hierarchy)
         x, info, status = hierarchy.solve(b.detach().contiguous(), options=options)
         if status != amg.AMG_OK:
             raise amg.AMGError(status, f"forward solve: {info}")

@@ -39,6 +39,11 @@ amg_opts resolve(const amg_opts* o) {
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 }  // namespace
 
+namespace amg {
+// For entry points defined in other translation units (amg_static.cu).
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace amg
+
 extern "C" {
 
 void amg_default_opts(amg_opts* o) {

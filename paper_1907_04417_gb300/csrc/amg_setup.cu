@@ -9,6 +9,7 @@
 #include <numeric>
 
 #include "amg_internal.cuh"
+#include "amg_local_svd.cuh"
 
 namespace amg {
 
@@ -117,11 +118,11 @@ __global__ void k_gather_w(int n, int m, const double* __restrict__ W, const int
   out[t] = W[(long long)r * n + perm[i]];
 }
 
-// Eq. (svd) for every aggregate: one warp per aggregate computes the thin
-// SVD of the n_a x m block by one-sided (Hestenes) Jacobi rotations on its
-// columns, sorts by singular value, keeps those above TOL*n_a/n_f (at least
-// one, at most min(n_a, m)), normalises them and flips each so that its
-// largest-magnitude entry (lowest row on ties) is positive.
+// Eq. (svd) for every aggregate: one warp per aggregate (local_svd_warp)
+// computes the thin SVD of the n_a x m block by one-sided (Hestenes) Jacobi
+// rotations on its columns, sorts by singular value, keeps those above
+// TOL*n_a/n_f (at least one, at most min(n_a, m)), normalises them and flips
+// each so that its largest-magnitude entry (lowest row on ties) is positive.
 __global__ void k_local_svd(const double* __restrict__ W, int m, int nagg,
                             const int* __restrict__ row_start, int nf, double tol,
                             double* __restrict__ work, double* __restrict__ U,
@@ -130,98 +131,7 @@ __global__ void k_local_svd(const double* __restrict__ W, int m, int nagg,
   int lane = threadIdx.x & 31;
   if (a >= nagg) return;
   int rs = row_start[a], na = row_start[a + 1] - rs;
-  const double* Wa = W + (size_t)rs * m;
-  double* X = work + (size_t)rs * m;
-  for (int t = lane; t < na * m; t += 32) X[t] = Wa[t];
-  __syncwarp();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    int rotated = 0;
-    for (int p = 0; p < m - 1; ++p) {
-      for (int q = p + 1; q < m; ++q) {
-        double al = 0, be = 0, ga = 0;
-        for (int i = lane; i < na; i += 32) {
-          double x = X[i * m + p], y = X[i * m + q];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          for (int i = lane; i < na; i += 32) {
-            double x = X[i * m + p], y = X[i * m + q];
-            X[i * m + p] = c * x - s * y;
-            X[i * m + q] = s * x + c * y;
-          }
-          rotated = 1;
-        }
-        __syncwarp();
-      }
-    }
-    if (!rotated) break;
-  }
-  double sig[16];
-  int idx[16];
-  for (int j = 0; j < m; ++j) {
-    double s = 0;
-    for (int i = lane; i < na; i += 32) s = fma(X[i * m + j], X[i * m + j], s);
-    sig[j] = sqrt(warp_sum(s));
-    idx[j] = j;
-  }
-  for (int j = 1; j < m; ++j) {  // stable insertion sort, descending
-    int v = idx[j];
-    int t = j;
-    while (t > 0 && sig[idx[t - 1]] < sig[v]) {
-      idx[t] = idx[t - 1];
-      --t;
-    }
-    idx[t] = v;
-  }
-  int rmax = na < m ? na : m;
-  double thr = tol * (double)na / (double)nf;
-  int r = 0;
-  for (int j = 0; j < rmax; ++j)
-    if (sig[idx[j]] > thr) ++r;
-  if (r == 0) r = 1;
-  for (int j = 0; j < r; ++j) {
-    int c = idx[j];
-    double s = sig[c];
-    bool zero = !(s > 0.0);
-    double scale = zero ? 0.0 : 1.0 / s;
-    double cst = 1.0 / sqrt((double)na);
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    double bv = 0;
-    for (int i = lane; i < na; i += 32) {
-      double v = zero ? cst : X[i * m + c] * scale;
-      double av = fabs(v);
-      if (av > best) {  // rows visited in increasing order: keeps the lowest on ties
-        best = av;
-        bi = i;
-        bv = v;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-        bv = ov;
-      }
-    }
-    double sgn = bv < 0 ? -1.0 : 1.0;
-    for (int i = lane; i < na; i += 32) {
-      double v = zero ? cst : X[i * m + c] * scale;
-      U[(size_t)(rs + i) * m + j] = sgn * v;
-    }
-  }
+  int r = local_svd_warp(W + (size_t)rs * m, m, na, nf, tol, work + (size_t)rs * m, U + (size_t)rs * m, lane);
   if (lane == 0) rkeep[a] = r;
 }
 

@@ -22,6 +22,11 @@
 #include <mutex>
 
 #include "../../include/amg.h"
+#include "amg_local_svd.cuh"
+
+namespace amg {
+void set_last_error(const char* msg);  // amg_capi.cu (thread-local message)
+}
 
 namespace {
 
@@ -32,9 +37,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_work_ptr[kMaxDevices] = {};
 int* g_flag_ptr[kMaxDevices] = {};
-// ``why`` documents each refusal in the source; the caller sees the status.
+// Every refusal leaves its reason for amg_last_error(), like the other
+// entry points; a successful call clears it.
 amg_status fail(amg_status s, const char* why) {
-  (void)why;
+  amg::set_last_error(why);
   return s;
 }
 
@@ -48,17 +54,9 @@ bool on_device(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-__device__ __forceinline__ double wsum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Same computation as the setup's per-aggregate SVD (one warp per aggregate:
-// one-sided Jacobi, descending singular values, TOL * n_a / n_f truncation,
-// at least one and at most min(n_a, m) columns, largest entry positive), with
-// every row range checked against the work area; a bad range sets the flag
-// and skips the aggregate.
+// The setup's per-aggregate computation (local_svd_warp: one warp per
+// aggregate), with every row range checked against the work area first; a
+// bad range sets the flag and skips the aggregate.
 __global__ void k_local_bases_static(const double* __restrict__ W, int m, int nagg,
                                      const int* __restrict__ row_start, int nf, double tol,
                                      double* __restrict__ work, double* __restrict__ U,
@@ -71,96 +69,8 @@ __global__ void k_local_bases_static(const double* __restrict__ W, int m, int na
     if (lane == 0) atomicOr(&g_basis_flag, 1);
     return;
   }
-  int na = re - rs;
-  const double* Wa = W + (size_t)rs * m;
-  double* X = work + (size_t)rs * m;
-  for (int t = lane; t < na * m; t += 32) X[t] = Wa[t];
-  __syncwarp();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    int rotated = 0;
-    for (int p = 0; p < m - 1; ++p) {
-      for (int q = p + 1; q < m; ++q) {
-        double al = 0, be = 0, ga = 0;
-        for (int i = lane; i < na; i += 32) {
-          double x = X[i * m + p], y = X[i * m + q];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = wsum(al);
-        be = wsum(be);
-        ga = wsum(ga);
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
-          double zeta = (be - al) / (2.0 * ga);
-          double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-          for (int i = lane; i < na; i += 32) {
-            double x = X[i * m + p], y = X[i * m + q];
-            X[i * m + p] = c * x - s * y;
-            X[i * m + q] = s * x + c * y;
-          }
-          rotated = 1;
-        }
-        __syncwarp();
-      }
-    }
-    if (!rotated) break;
-  }
-  double sig[16];
-  int idx[16];
-  for (int j = 0; j < m; ++j) {
-    double s = 0;
-    for (int i = lane; i < na; i += 32) s = fma(X[i * m + j], X[i * m + j], s);
-    sig[j] = sqrt(wsum(s));
-    idx[j] = j;
-  }
-  for (int j = 1; j < m; ++j) {
-    int v = idx[j], t = j;
-    while (t > 0 && sig[idx[t - 1]] < sig[v]) {
-      idx[t] = idx[t - 1];
-      --t;
-    }
-    idx[t] = v;
-  }
-  int rmax = na < m ? na : m;
-  double thr = tol * (double)na / (double)nf;
-  int r = 0;
-  for (int j = 0; j < rmax; ++j)
-    if (sig[idx[j]] > thr) ++r;
-  if (r == 0) r = 1;
-  for (int j = 0; j < r; ++j) {
-    int c = idx[j];
-    double s = sig[c];
-    bool zero = !(s > 0.0);
-    double scale = zero ? 0.0 : 1.0 / s;
-    double cst = 1.0 / sqrt((double)na);
-    double best = -1.0, bv = 0;
-    int bi = 0x7fffffff;
-    for (int i = lane; i < na; i += 32) {
-      double v = zero ? cst : X[i * m + c] * scale;
-      if (fabs(v) > best) {
-        best = fabs(v);
-        bi = i;
-        bv = v;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-        bv = ov;
-      }
-    }
-    double sgn = bv < 0 ? -1.0 : 1.0;
-    for (int i = lane; i < na; i += 32) {
-      double v = zero ? cst : X[i * m + c] * scale;
-      U[(size_t)(rs + i) * m + j] = sgn * v;
-    }
-  }
+  int r = amg::local_svd_warp(W + (size_t)rs * m, m, re - rs, nf, tol, work + (size_t)rs * m,
+                              U + (size_t)rs * m, lane);
   if (lane == 0) rkeep[a] = r;
 }
 
@@ -169,6 +79,7 @@ __global__ void k_local_bases_static(const double* __restrict__ W, int m, int na
 extern "C" amg_status amg_local_bases_static(const double* W, int32_t m, const int32_t* row_start,
                                              int32_t nagg, int32_t nf, double tol, double* U,
                                              int32_t* r, void* stream) {
+  amg::set_last_error("");
   if (m < 1 || m > 16) return fail(AMG_ERR_INVALID_ARG, "m must be in [1, 16]");
   if (nagg < 1 || nf < 1) return fail(AMG_ERR_INVALID_ARG, "nagg and nf must be positive");
   if ((long long)nf * m > AMG_LOCAL_BASES_STATIC_DOUBLES)

@@ -94,3 +94,20 @@ def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     fields = r.stdout.split()
     assert fields[:6] == ["1", "1", "64", "0", "0", "1"], r.stdout
+
+
+def test_static_bases_refusals_leave_their_reason(lib):
+    """The allocation-free entry point records why it refused (argument
+    checks run before any CUDA call), and a later refusal replaces the
+    message of an earlier one."""
+    assert lib.amg_solve(None, None, None, 1, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "non-null" in amg.last_error()
+    assert lib.amg_local_bases_static(None, 0, None, 1, 1, 0.1, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "m must be in [1, 16]" in amg.last_error()
+    assert lib.amg_local_bases_static(None, 4, None, 0, 1, 0.1, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "nagg and nf must be positive" in amg.last_error()
+    big = (1 << 17) // 4 + 1
+    assert lib.amg_local_bases_static(None, 4, None, 1, big, 0.1, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "work area" in amg.last_error()
+    assert lib.amg_local_bases_static(None, 4, None, 1, 16, -1.0, None, None, None) == amg.AMG_ERR_INVALID_ARG
+    assert "tol" in amg.last_error()

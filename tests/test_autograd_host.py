@@ -1,6 +1,7 @@
 """Host-side pieces of the differentiable solve: the torch assembly of the
 cell-centred operator matches the numpy one and differentiates correctly."""
 import numpy as np
+import pytest
 import torch
 
 from paper_1907_04417_gb300.autograd import CellCentredDiffusion
@@ -32,3 +33,30 @@ def test_torch_assembly_jacobian_vector_product():
         km = kk.copy().ravel(); km[c] -= h
         fd = (problems.cc5(N, kp.reshape(N, N)).data - problems.cc5(N, km.reshape(N, N)).data) @ w.numpy() / (2 * h)
         np.testing.assert_allclose(g[c], fd, rtol=1e-7)
+
+
+class _FakeHierarchy:
+    """Stands in for a device hierarchy: only the values it was set up with."""
+
+    def __init__(self, values):
+        self.setup_values = values
+
+    def solve(self, *a, **k):  # pragma: no cover - must not be reached
+        raise AssertionError("a refused forward must not solve")
+
+
+def test_forward_refuses_changed_values():
+    from paper_1907_04417_gb300.autograd import AMGSolve, check_values
+    N = 5
+    asm = CellCentredDiffusion(N)
+    k = torch.from_numpy(problems.lognormal_field(N, 1.0, seed=1))
+    v = asm.values(k)
+    H = _FakeHierarchy(v.numpy().copy())
+    check_values(v, H)                                 # the same values pass
+    v2 = v.clone()
+    v2[3] *= 1.0 + 1e-12
+    b = torch.ones(N * N, dtype=torch.float64)
+    with pytest.raises(ValueError, match="differ"):
+        AMGSolve.apply(v2.requires_grad_(True), b, H, None)
+    with pytest.raises(ValueError, match="differ"):
+        check_values(v[:-1], H)
