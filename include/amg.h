@@ -289,8 +289,13 @@ enum {
   AMG_KERNEL_SMOOTH_L0 = 3,      /* post-smoothing with r.z     (level 0)          */
   AMG_KERNEL_PROLONG_L0 = 4,     /* x += P e                    (level 0)          */
   AMG_KERNEL_CG_UPDATE = 5,      /* x, r update with ||r||      (level 0)          */
-  AMG_KERNEL_GS_L0 = 6           /* one backward Gauss-Seidel sweep, all colours
+  AMG_KERNEL_GS_L0 = 6,          /* one backward Gauss-Seidel sweep, all colours
                                     (level 0, smoother 1; the last post-sweep)      */
+  AMG_KERNEL_CG_DIRECTION = 7,   /* p = z + beta p (with x += alpha p in the
+                                    double-float mode)          (level 0)          */
+  AMG_KERNEL_COARSE_LEVELS = 8   /* every launch of one V-cycle on levels >= 1,
+                                    timed as one span (after the level-0
+                                    restriction, before the level-0 prolongation) */
 };
 amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
 amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);

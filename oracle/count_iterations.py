@@ -12,6 +12,13 @@ With --bootstrap the smooth vectors come from the oracle's own bootstrap
 With --variant (gs/V, l1jacobi/K or gs/K) the preconditioner is that cycle
 variant (Section 5: Gauss-Seidel smoothing, K-cycles) instead of the
 l1-Jacobi V-cycle; the key gains the suffix _<smoother><kind>.
+
+    python oracle/count_iterations.py --workload=poisson|jump|elasticity|cc
+
+records the counts of the other seeded workloads at their full sizes (the
+first right-hand side of each system): the 64^2 Poisson problem, the 128^3
+jumping-coefficient problem, every member of the uneven elasticity batch and
+the 512^2 cell-centred diffusion problem.
 """
 import json
 import os
@@ -75,7 +82,48 @@ def main(grids, bootstrap=False, variant=None):
         print(key, data[key], flush=True)
 
 
+def record(data, key, P, note):
+    t0 = time.time()
+    H = O.setup(P.A, P.aggs, P.n_nodes, P.W)
+    ts = time.time() - t0
+    t0 = time.time()
+    x, res = O.solve(H, P.B[:, 0], maxit=5000)
+    tsol = time.time() - t0
+    b = P.B[:, 0]
+    data[key] = {
+        "iters": res[0].iters, "converged": bool(res[0].converged), "relres": res[0].relres,
+        "true_relres": float(np.linalg.norm(b - P.A @ x) / np.linalg.norm(b)),
+        "levels": [l.A.shape[0] for l in H.levels], "opc": O.operator_complexity(H),
+        "setup_s": ts, "solve_s": tsol, "rtol": 1e-8, "note": note,
+    }
+    json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
+    print(key, data[key], flush=True)
+
+
+def main_workload(which):
+    data = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    if which == "poisson":
+        P = inputs.poisson(N=64, nrhs=1)
+        record(data, P.name, P, "FP64 oracle, zero initial guess, first RHS (seed 1001, uniform[-1,1])")
+    elif which == "jump":
+        P = inputs.jumping3d(N=128, nrhs=32)
+        record(data, P.name, P, "FP64 oracle, zero initial guess, first of the 32 RHS (seed 1003, standard normal)")
+    elif which == "cc":
+        P = inputs.diffusion_cc(N=512, nrhs=8)
+        record(data, P.name, P, "FP64 oracle, zero initial guess, first of the 8 RHS (seed 1005, uniform[-1,1])")
+    elif which == "elasticity":
+        for s, P in enumerate(inputs.elasticity_batch()):
+            record(data, f"{P.name}_member{s}", P,
+                   f"FP64 oracle, zero initial guess, first RHS of batch member {s} (seed {1004 + 100 * s})")
+    else:
+        raise SystemExit(f"unknown workload {which}")
+
+
 if __name__ == "__main__":
+    wl = next((a.split("=", 1)[1] for a in sys.argv[1:] if a.startswith("--workload=")), None)
+    if wl:
+        main_workload(wl)
+        sys.exit(0)
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     var = next((a.split("=", 1)[1] for a in sys.argv[1:] if a.startswith("--variant=")), None)
     main([int(a) for a in args] or [1024], bootstrap="--bootstrap" in sys.argv, variant=var)

@@ -33,6 +33,8 @@ KERNEL_SMOOTH_L0 = 3
 KERNEL_PROLONG_L0 = 4
 KERNEL_CG_UPDATE = 5
 KERNEL_GS_L0 = 6
+KERNEL_CG_DIRECTION = 7
+KERNEL_COARSE_LEVELS = 8
 
 
 class AMGError(RuntimeError):

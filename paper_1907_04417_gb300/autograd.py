@@ -7,8 +7,8 @@ A^{-T} = A^{-1}), followed by the fused kernel that writes
 dL/da_ij = -sum_c lambda[i, c] x[j, c] for every stored entry of A.  The
 gradient with respect to b is lambda.  ``values`` must hold A's CSR values in
 the CSR order the hierarchy was set up with, and equal them: the forward
-solve refuses values that differ from the hierarchy's (a changed matrix needs
-a new Hierarchy).  The hierarchy is a constant preconditioner (the derivative
+solve refuses values that differ from the hierarchy's by more than rounding
+(a changed matrix needs a new Hierarchy).  The hierarchy is a constant preconditioner (the derivative
 of the exact solution does not depend on it).
 
 ``CellCentredDiffusion`` assembles the cell-centred 5-point operator of the
@@ -24,16 +24,25 @@ from . import amg
 from .hostsetup import problems
 
 
+VALUES_RTOL = 1e-12
+
+
 def check_values(values, hierarchy):
     """Refuse a solve whose matrix values differ from those the hierarchy was
     set up with: the forward solve and the gradient would belong to the old
     matrix.  A caller that changes A (an optimisation step on the
-    coefficients) builds a new Hierarchy."""
+    coefficients) builds a new Hierarchy.  Differences of rounding size (two
+    assemblies of the same coefficients, at most VALUES_RTOL of the largest
+    entry) are accepted."""
     ref = hierarchy.setup_values
     v = values.detach()
     if isinstance(ref, np.ndarray):
         ref = torch.from_numpy(ref)
-    if v.shape != ref.shape or not torch.equal(v.to(device=ref.device, dtype=ref.dtype), ref):
+    if v.shape != ref.shape:
+        raise ValueError("values differ from the matrix the hierarchy was set up with (size); "
+                         "build a new Hierarchy for the new matrix")
+    d = (v.to(device=ref.device, dtype=ref.dtype) - ref).abs().max()
+    if not bool(d <= VALUES_RTOL * ref.abs().max()):
         raise ValueError("values differ from the matrix the hierarchy was set up with; "
                          "build a new Hierarchy for the new matrix")
 

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 
 #include "amg_launch.cuh"
 
@@ -1698,7 +1699,10 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     oth[k] = static_cast<TC*>(W.v[k]);
   }
   auto F = [&](int k) { return static_cast<TC*>(W.f[k]); };
+  // levels >= 1 timed as one span (AMG_KERNEL_COARSE_LEVELS)
+  std::unique_ptr<TimedLaunch> coarse_span;
   for (int k = 0; k + 1 < L; ++k) {
+    if (k == 1) coarse_span.reset(new TimedLaunch(h, AMG_KERNEL_COARSE_LEVELS, st, pool));
     for (int s = 1; s < W.pre; ++s) {
       launch_smooth<TC>(K, W.nzl[k], P.lev[k], W.rp[k], F(k), cur[k], oth[k], done, st);
       std::swap(cur[k], oth[k]);
@@ -1719,9 +1723,11 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
       }
     }
   }
+  if (!coarse_span) coarse_span.reset(new TimedLaunch(h, AMG_KERNEL_COARSE_LEVELS, st, pool));
   launch_coarse<TC>(K, P.co, F(L - 1), cur[L - 1], done, st);
   TC* res = cur[L - 1];
   for (int k = L - 2; k >= 0; --k) {
+    if (k == 0) coarse_span.reset();
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_PROLONG_L0 : -1, st, pool);
       if (k == 0 && W.u0free)  // u = D^{-1} f + P e
@@ -1888,6 +1894,7 @@ static void enqueue_iteration(amg_hierarchy* h, Plan& P, Workspace& W, cudaStrea
     enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
     if (P.L == 1) launch_rz(W, L0, 1, st);
   }
+  TimedLaunch tl(h, AMG_KERNEL_CG_DIRECTION, st, pool);
   launch_cg_p(P, W, L0, 0, st);
 }
 

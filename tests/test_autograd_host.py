@@ -54,7 +54,8 @@ def test_forward_refuses_changed_values():
     H = _FakeHierarchy(v.numpy().copy())
     check_values(v, H)                                 # the same values pass
     v2 = v.clone()
-    v2[3] *= 1.0 + 1e-12
+    v2[3] *= 1.0 + 1e-9
+    check_values(v * (1.0 + 1e-15), H)                 # rounding-size differences pass
     b = torch.ones(N * N, dtype=torch.float64)
     with pytest.raises(ValueError, match="differ"):
         AMGSolve.apply(v2.requires_grad_(True), b, H, None)
