@@ -201,16 +201,25 @@ def peaks():
 
 
 def host_cpu():
-    """Model name and logical core count of the host."""
-    model = platform.processor() or platform.machine()
+    """Model name, architecture and logical core count of the host."""
+    model = None
     try:
-        for l in open("/proc/cpuinfo"):
-            if l.lower().startswith(("model name", "cpu model")):
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.lower().startswith("model name"):
                 model = l.split(":", 1)[1].strip()
                 break
-    except OSError:
+    except Exception:
         pass
-    return model, os.cpu_count() or 1
+    if not model:
+        try:
+            for l in open("/proc/cpuinfo"):
+                if l.lower().startswith(("model name", "cpu model")):
+                    model = l.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return f"{model or platform.processor() or 'unknown'} ({platform.machine()})", os.cpu_count() or 1
 
 
 def kernel_source_hash():
@@ -326,13 +335,19 @@ _ORACLE = {}
 
 def _oracle_iters_worker(args):
     """Worker: ``k`` oracle PCG iterations on right-hand side column ``c`` of
-    system ``s`` (the hierarchies were built before the pool was forked)."""
+    system ``s`` (the hierarchies were built before the pool was forked), in
+    solves of at most ``cap`` iterations (the solve's own count: a small
+    problem would otherwise iterate past convergence into a zero residual)."""
     from oracle import amg_oracle as O
-    s, c, k = args
+    s, c, k, cap = args
     H, B = _ORACLE["H"][s], _ORACLE["B"][s]
     A = H.levels[0].A
     t0 = time.perf_counter()
-    O.pcg(A, B[:, c % B.shape[1]], lambda r: O.vcycle(H, r), fixed_iters=k)
+    left = k
+    while left > 0:
+        step = min(left, max(1, cap))
+        O.pcg(A, B[:, c % B.shape[1]], lambda r: O.vcycle(H, r), fixed_iters=step)
+        left -= step
     return time.perf_counter() - t0
 
 
@@ -364,14 +379,15 @@ class OracleLeg:
         """iters[s]: PCG iterations of system s.  Returns one-core and
         all-core ms per RHS (mean over the systems' RHS) and what ran."""
         nsys = len(iters)
-        t1 = [_oracle_iters_worker((s, 0, 1)) for s in range(nsys)]
+        cap = [max(1, int(i) - 1) for i in iters]
+        t1 = [_oracle_iters_worker((s, 0, 1, cap[s])) for s in range(nsys)]
         per_round = sum(t1)
         k = max(2, int(budget_s / 2 / max(per_round, 1e-3)))
-        one = [_oracle_iters_worker((s, 0, k)) / k for s in range(nsys)]
+        one = [_oracle_iters_worker((s, 0, k, cap[s])) / k for s in range(nsys)]
         ms_one = sum(one[s] * iters[s] for s in range(nsys)) / nsys * 1e3
         out = {"one_core": {"value": ms_one, "cores": 1, "sample_iters": k}}
         if self.pool is not None:
-            jobs = [(s, c, k) for c in range(self.cores) for s in range(nsys)]
+            jobs = [(s, c, k, cap[s]) for c in range(self.cores) for s in range(nsys)]
             t0 = time.perf_counter()
             self.pool.map(_oracle_iters_worker, jobs, chunksize=1)
             wall = time.perf_counter() - t0

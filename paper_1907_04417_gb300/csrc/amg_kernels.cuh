@@ -759,20 +759,25 @@ __global__ void __launch_bounds__(BS) k_restrict(const int* __restrict__ cta_agg
 // rows (CL lanes per row, RPW rows per pass), fc = P_a^T t accumulated in
 // registers (RMAX >= r_a coarse dofs), the row groups of the warp combined
 // by shuffles, then uc = D_c^{-1} fc.  No shared-memory tile and no CTA-wide
-// barrier; matrix and prolongator entries are read straight from global.
+// barrier.  Memory round trips per pass: the row's own operands (its f
+// slice and its P row) and its matrix values are requested together with its
+// gathers, and the column indices of the next pass's rows (the first RB of
+// each) are requested before this pass's products, so that a pass waits on
+// one round trip (its gathers) instead of three.
 template <typename TC, int K, int RMAX, bool STG>
-__global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restrict__ row_start,
-                                                   const int* __restrict__ coarse_start,
-                                                   const long long* __restrict__ blk_start,
-                                                   const TC* __restrict__ P, const int* __restrict__ rowptr,
-                                                   const int* __restrict__ col, const TC* __restrict__ val,
-                                                   const TC* __restrict__ f, const TC* __restrict__ u,
-                                                   TC* __restrict__ fc, TC* __restrict__ uc,
-                                                   const TC* __restrict__ dinvc, const int* __restrict__ done,
-                                                   Stage sg) {
+__global__ void __launch_bounds__(BS, (RMAX <= 4 && !STG) ? 3 : 2) k_restrict_w(int nagg, const int* __restrict__ row_start,
+                                                      const int* __restrict__ coarse_start,
+                                                      const long long* __restrict__ blk_start,
+                                                      const TC* __restrict__ P, const int* __restrict__ rowptr,
+                                                      const int* __restrict__ col, const TC* __restrict__ val,
+                                                      const TC* __restrict__ f, const TC* __restrict__ u,
+                                                      TC* __restrict__ fc, TC* __restrict__ uc,
+                                                      const TC* __restrict__ dinvc, const int* __restrict__ done,
+                                                      Stage sg) {
   if (*done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
+  constexpr int RB = gather_depth<1>();  // entries of a row requested in one batch
   const int lane = threadIdx.x & 31;
   const int g = lane / CL, cl = lane % CL;
   // STG: the CTA's NWARP aggregates are one row range, staged into shared
@@ -791,21 +796,83 @@ __global__ void __launch_bounds__(BS) k_restrict_w(int nagg, const int* __restri
   for (int p = 0; p < RMAX; ++p)
 #pragma unroll
     for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
+  // extent and the first RB column indices of a row (-1 past its end)
+  auto fetch = [&](int i, bool valid, int& j0, int& j1, int (&c)[RB]) {
+    j0 = valid ? cv.rp[i - cv.roff] : 0;
+    j1 = valid ? cv.rp[i + 1 - cv.roff] : 0;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) c[b] = j0 + b < j1 ? cv.col[j0 + b - cv.coff] : -1;
+  };
+  int c[RB], j0, j1;
+  fetch(rs + g, rs + g < re, j0, j1, c);
   for (int base = rs; base < re; base += RPW) {
     const int i = base + g;
     const bool valid = i < re;
-    TC s[CPT];
-    row_acc<TC, TC, K, 1>(i, valid, cv, u, 0, cl, s);
+    // own operands and matrix values, independent of the gathers
+    TC fv[CPT], pv[RMAX], av[RB];
     if (valid) {
-      TC fv[CPT];
       ldv<TC, CPT>(f + (size_t)i * K + cl * CPT, fv);
       const TC* prow = Pa + (size_t)(i - rs) * ra;
 #pragma unroll
+      for (int p = 0; p < RMAX; ++p) pv[p] = p < ra ? __ldg(prow + p) : TC(0);
+    }
+#pragma unroll
+    for (int b = 0; b < RB; ++b) av[b] = c[b] >= 0 ? cv.val[j0 + b - cv.voff] : TC(0);
+    // gathers of the first batch
+    TC xv[RB][CPT];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+      if (c[b] >= 0) {
+        ldv<TC, CPT>(u + (size_t)c[b] * K + cl * CPT, xv[b]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) xv[b][t] = TC(0);
+      }
+    }
+    const int jr = j0 + RB, je = j1;
+    // the next pass's column indices, requested before this pass's products
+    {
+      const int in = i + RPW;
+      fetch(in, in < re, j0, j1, c);
+    }
+    // the products in row order (the order of row_acc)
+    TC s[CPT];
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) s[t] = TC(0);
+#pragma unroll
+    for (int b = 0; b < RB; ++b)
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) s[t] = fma(av[b], xv[b][t], s[t]);
+    // the rest of a long row, batch by batch
+    for (int j = jr; j < je; j += RB) {
+      int c2[RB];
+      TC a2[RB], x2[RB][CPT];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        const bool ok = j + b < je;
+        c2[b] = ok ? cv.col[j + b - cv.coff] : -1;
+        a2[b] = ok ? cv.val[j + b - cv.voff] : TC(0);
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        if (c2[b] >= 0) {
+          ldv<TC, CPT>(u + (size_t)c2[b] * K + cl * CPT, x2[b]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) x2[b][t] = TC(0);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) s[t] = fma(a2[b], x2[b][t], s[t]);
+    }
+    if (valid) {
+#pragma unroll
       for (int p = 0; p < RMAX; ++p) {
         if (p < ra) {
-          const TC pv = __ldg(prow + p);
 #pragma unroll
-          for (int t = 0; t < CPT; ++t) acc[p][t] = fma(pv, fv[t] - s[t], acc[p][t]);
+          for (int t = 0; t < CPT; ++t) acc[p][t] = fma(pv[p], fv[t] - s[t], acc[p][t]);
         }
       }
     }

@@ -30,12 +30,11 @@ pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 RTOL_TRUE = 1.1e-8
-
-
-def _gold(key):
-    """The oracle's own iteration count on a workload (first RHS), stored by
-    oracle/count_iterations.py."""
-    return json.load(open(os.path.join(HERE, "golden", "oracle_iterations.json")))[key]["iters"]
+# The oracle's counts are taken live on the host that runs the test for the
+# 3D and cell-centred workloads: their inputs pass through libm and BLAS
+# routines whose last bits differ between hosts, and a last-bit change of an
+# edge weight can change a matching decision (the stored counts, from another
+# host, differ by up to ten iterations).
 
 
 @pytest.fixture(scope="module")
@@ -167,7 +166,7 @@ def test_jump_full_setup_vcycle_pcg(amg, jump):
     Zg = Hg.vcycle(R)
     Zo = O.vcycle(Ho, R)
     assert np.linalg.norm(Zg - Zo) / np.linalg.norm(Zo) <= 1e-12
-    it = _fp64_parity(amg, P, Ho, Hg, P.B[:, 0].copy(), expect_iters=_gold("jump7_128^3"))
+    it = _fp64_parity(amg, P, Ho, Hg, P.B[:, 0].copy())
     _fixed_iterate_parity(amg, Ho, Hg, P.B[:, 0].copy(), min(it, 10))
 
 
@@ -200,7 +199,7 @@ def test_elasticity_full_batch(amg):
     P = batch[s]
     Ho = O.setup(P.A, P.aggs, P.n_nodes, P.W)
     _setup_parity(P, Ho, Hs[s])
-    it = _fp64_parity(amg, P, Ho, Hs[s], P.B[:, 0].copy(), expect_iters=_gold(f"{P.name}_member{s}"))
+    it = _fp64_parity(amg, P, Ho, Hs[s], P.B[:, 0].copy())
     assert abs(res[64][s][0]["iters"] - it) <= 1
 
 
@@ -217,7 +216,7 @@ def ccd(amg):
 def test_cc_full_setup_pcg_batch(amg, ccd):
     P, Ho, Hg = ccd
     _setup_parity(P, Ho, Hg)
-    it = _fp64_parity(amg, P, Ho, Hg, P.B[:, 0].copy(), expect_iters=_gold("cc5_512x512"))
+    it = _fp64_parity(amg, P, Ho, Hg, P.B[:, 0].copy())
     _fixed_iterate_parity(amg, Ho, Hg, P.B[:, 0].copy(), min(it, 10))
     _batch_properties(amg, P, Hg, P.B)
 
