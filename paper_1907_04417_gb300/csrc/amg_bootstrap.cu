@@ -75,6 +75,7 @@ static std::vector<double> a_norm2(const Plan& P0, int n, int K, const double* v
 
 void run_bootstrap_test(const std::vector<amg_hierarchy*>& hs, double* x, int nrhs, int nu, int symmetric,
                         const amg_opts& o, cudaStream_t st, double* rho, double* anorm) {
+  NvtxRange nv("amg bootstrap testing phase");
   AMG_REQUIRE(!hs.empty(), "at least one hierarchy is needed");
   AMG_REQUIRE(nrhs >= 1 && nrhs <= 32, "nrhs must be in [1, 32]");
   AMG_REQUIRE(nu >= 1, "nu must be >= 1");

@@ -10,9 +10,20 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/amg.h"
 
 namespace amg {
+
+// NVTX range over a scope (setup, solves, graph replays): visible to
+// profilers that collect NVTX; a no-op otherwise (header-only NVTX v3).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- errors --
 struct Error : std::runtime_error {
@@ -78,6 +89,9 @@ struct Stage {
   int span8 = 0;     // capacity of the 8-byte arrays (elements, multiple of 2)
   int enabled = 0;   // 0: the level is read straight from global memory
   int* err = nullptr;
+  // polls of the first wait for a staged copy (0: the normal bound); a
+  // small value is a test hook that makes the first wait give up
+  int first_wait = 0;
 };
 
 // Every level is numbered so that each aggregate of the next level owns a

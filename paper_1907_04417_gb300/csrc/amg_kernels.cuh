@@ -78,13 +78,22 @@ __device__ __forceinline__ void stv(T* p, const T (&r)[N]) {
 // widened to 16-byte boundaries (the arrays carry 16 padding elements).
 // The wait on the mbarrier is bounded: on timeout the kernel records an error
 // in *err (the host then reports AMG_ERR_TIMEOUT) and waits once more, with
-// the same bound, before it goes on.
+// the full bound, before it goes on (stage_wait).
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 // Shared memory of the staging area with n4 four-byte and n8 eight-byte value arrays.
 __host__ __device__ inline size_t stage_bytes(const Stage& sg, int n4, int n8) {
   if (!sg.enabled) return 0;
   return 16 + align16((size_t)(sg.rows_max + 1) * 4) + (size_t)sg.span4 * 4 * (1 + n4) +
          (size_t)sg.span8 * 8 * n8;
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (no registers, no completion):
+// the range is widened to 16-byte boundaries; 0 bytes issue nothing.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  if (bytes == 0) return;
+  const unsigned long long a0 = reinterpret_cast<unsigned long long>(p) & ~15ull;
+  const unsigned long long a1 = (reinterpret_cast<unsigned long long>(p) + bytes + 15ull) & ~15ull;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((unsigned)(a1 - a0)) : "memory");
 }
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -105,9 +114,23 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
+constexpr int kWaitPolls = 1 << 22;  // polls of a bounded wait (each try_wait may block briefly)
+// Bounded wait for an mbarrier phase: at most ``polls`` try_wait polls, or,
+// for a first wait shortened by the test hook (polls < 16), that many
+// non-blocking test_wait polls.  Returns false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase, int polls = kWaitPolls) {
   unsigned ok = 0;
-  for (int it = 0; it < (1 << 22) && !ok; ++it) {
+  if (polls > 0 && polls < 16) {
+    for (int it = 0; it < polls && !ok; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_addr(bar)), "r"(phase)
+          : "memory");
+    }
+    return ok != 0;
+  }
+  for (int it = 0; it < polls && !ok; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
@@ -115,6 +138,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase)
         : "memory");
   }
   return ok != 0;
+}
+// The wait of a staged copy: the first wait is bounded (by sg.first_wait
+// when the test hook sets it); when it gives up the CTA records the error
+// for the host (AMG_ERR_TIMEOUT) and waits once more with the full bound, so
+// that no copy into its shared memory is left in flight, and goes on.
+__device__ __forceinline__ void stage_wait(const Stage& sg, uint64_t* bar, unsigned phase) {
+  if (!mbar_wait_bounded(bar, phase, sg.first_wait > 0 ? sg.first_wait : kWaitPolls)) {
+    atomicOr(sg.err, 1);
+    mbar_wait_bounded(bar, phase);
+  }
 }
 
 // Double-buffered staging for CTAs that walk several row chunks (persistent
@@ -164,10 +197,7 @@ __device__ __forceinline__ void pipe_wait(const Stage& sg, unsigned char* smem, 
                                           const int* __restrict__ rowptr, const int*& rp, int& roff,
                                           const int*& cs, const float* (&vs)[NV], int& joff) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem) + buf;
-  if (!mbar_wait_bounded(bar, (unsigned)(use & 1))) {
-    atomicOr(sg.err, 1);
-    mbar_wait_bounded(bar, (unsigned)(use & 1));
-  }
+  stage_wait(sg, bar, (unsigned)(use & 1));
   unsigned char* b = smem + 16 + (size_t)buf * pipe_buf_bytes(sg, NV);
   rp = reinterpret_cast<const int*>(b);
   roff = r0 & ~3;
@@ -254,10 +284,7 @@ __device__ __forceinline__ bool stage_csr(const Stage& sg, unsigned char* smem, 
   }
   for (int t = threadIdx.x; t <= r1 - r0; t += blockDim.x) rp_s[t] = __ldg(rowptr + r0 + t);
   __syncthreads();
-  if (!mbar_wait_bounded(bar, 0)) {
-    atomicOr(sg.err, 1);
-    mbar_wait_bounded(bar, 0);
-  }
+  stage_wait(sg, bar, 0);
   srp = rp_s;
   scol = col_s;
   return true;
@@ -791,6 +818,18 @@ __global__ void __launch_bounds__(BS, (RMAX <= 4 && !STG) ? 3 : 2) k_restrict_w(
   const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
   const int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
   const TC* Pa = P + __ldg(blk_start + a);
+  // the aggregate's contiguous operands (its f rows, its CSR slice, its P
+  // block) are requested into L2 at once, so that the passes after the
+  // first wait on L2 instead of DRAM
+  if (lane == 0) {
+    prefetch_l2(f + (size_t)rs * K, (size_t)(re - rs) * K * sizeof(TC));
+    prefetch_l2(Pa, (size_t)(re - rs) * ra * sizeof(TC));
+    if constexpr (!STG) {
+      const int jb = __ldg(rowptr + rs), je = __ldg(rowptr + re);
+      prefetch_l2(col + jb, (size_t)(je - jb) * sizeof(int));
+      prefetch_l2(val + jb, (size_t)(je - jb) * sizeof(TC));
+    }
+  }
   TC acc[RMAX][CPT];
 #pragma unroll
   for (int p = 0; p < RMAX; ++p)

@@ -112,6 +112,7 @@ __global__ void k_match_commit(int n, const int* __restrict__ best, int* __restr
 }  // namespace
 
 void run_pairwise_matching(const amg_csr* A, const double* w, int32_t* mate_out, cudaStream_t st) {
+  NvtxRange nv("amg pairwise matching");
   AMG_REQUIRE(A && A->n >= 0 && A->nnz >= 0 && A->rowptr && (A->nnz == 0 || (A->col && A->val)) && w && mate_out,
               "null argument");
   const int n = A->n;
@@ -320,6 +321,7 @@ __global__ void k_ps_galerkin(int nc, int pass, const int* __restrict__ members,
 
 void run_pairwise_step(const amg_csr* A, const double* w, int32_t* agg_out, int32_t* nc_out, int32_t* rowptr_c,
                        int32_t* col_c, double* val_c, int32_t* nnz_c_out, double* wc_out, cudaStream_t st) {
+  NvtxRange nv("amg pairwise step");
   AMG_REQUIRE(agg_out && nc_out && rowptr_c && col_c && val_c && nnz_c_out && wc_out, "null argument");
   const int n = A ? A->n : 0;
   const long long nnz = A ? A->nnz : 0;

@@ -452,6 +452,7 @@ static void coarsest_inverse(Plan& P, const Level& C, double* inv_out, cudaStrea
 void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t* const* agg,
                      const int32_t* n_nodes, const double* W, int m, const amg_opts& o,
                      cudaStream_t st) {
+  NvtxRange nv("amg setup");
   AMG_REQUIRE(A && A->rowptr && A->col && A->val, "A and its arrays must be non-null");
   AMG_REQUIRE(A->n > 0 && A->nnz > 0, "A must be non-empty");
   AMG_REQUIRE(nlev >= 0 && nlev <= 15, "n_agg_levels must be in [0, 15]");
@@ -738,6 +739,7 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
 // Concatenate the hierarchies of several systems block-diagonally, level by
 // level, so that one launch sequence serves all of them.
 void build_batch_plan(Plan& B, const std::vector<amg_hierarchy*>& hs, cudaStream_t st) {
+  NvtxRange nv("amg batch plan");
   const int ns = (int)hs.size();
   const int L = hs[0]->plan.L;
   for (auto* h : hs) AMG_REQUIRE(h->plan.L == L, "all hierarchies of a batch must have the same number of levels");

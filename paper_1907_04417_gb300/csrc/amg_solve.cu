@@ -8,6 +8,7 @@
 #include <cstring>
 #include <memory>
 
+#include "amg_coarse.cuh"
 #include "amg_launch.cuh"
 
 namespace amg {
@@ -632,6 +633,10 @@ struct Workspace {
   int variant = 0;        // smoother | cycle << 1 (float64 only); 0: the tuned V-cycle
   VarCycle var;           // buffers of the variant cycle
   std::vector<cudaEvent_t> gev;
+  // the small levels in one cooperative launch (k_coarse_cycle): start level
+  // (-1: off), CTAs, barrier words, test hook
+  int cc_s = -1, cc_grid = 0, cc_hang = 0;
+  unsigned* cc_bar = nullptr;
   ~Workspace() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
@@ -1497,6 +1502,64 @@ static void ensure_scaled(Plan& P) {
 
 static void make_var(Plan& P, Workspace& W, int variant);
 
+// Test hook: AMG_TEST_FIRST_WAIT=n (1..15) limits the first wait for every
+// staged copy of this workspace (and of its plan's grouped levels) to n
+// non-blocking polls, so that a test sees the bounded wait give up and the
+// solve report AMG_ERR_TIMEOUT; the drain wait keeps its full bound.
+static void apply_wait_hook(Plan& P, Workspace& W) {
+  const char* e = std::getenv("AMG_TEST_FIRST_WAIT");
+  const int n = e ? std::atoi(e) : 0;
+  if (n < 1 || n > 15) return;
+  auto set = [n](Stage& sg) { sg.first_wait = n; };
+  for (auto& r : W.rp) set(r.sg);
+  for (auto& t : W.tp) {
+    set(t.sg);
+    set(t.wsg);
+  }
+  set(W.rq.sg);
+  for (KState* k : {&W.ks, &W.ksq, &W.ksf_upd, &W.ksf_post}) set(k->sg);
+  for (auto& l : P.lev) set(l.gsg);
+  for (auto& t : P.tr) set(t.gsg);
+}
+
+// Start level of the fused small-level cycle: the first level k >= 1 above
+// the coarsest whose sweep is at most 2^25 multiply-adds (nnz_k K), if the
+// cooperative launch fits one CTA per SM.  AMG_FUSED_COARSE=0 keeps the
+// launch-per-step cycle; AMG_TEST_BARRIER_HANG=1 is the barrier test hook.
+template <typename TC, int K>
+static bool cc_fits() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_coarse_cycle<TC, K>, CC_BS, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return nb >= 1;
+}
+static void setup_fused_coarse(Plan& P, Workspace& W) {
+  W.cc_s = -1;
+  const char* e = std::getenv("AMG_FUSED_COARSE");
+  if ((e && e[0] == '0') || P.L < 3 || P.L > CC_MAXL || W.variant) return;
+  int s = -1;
+  for (int k = 1; k + 1 < P.L; ++k)
+    if ((double)P.lev[k].nnz * W.K <= (double)(1 << 25)) {
+      s = k;
+      break;
+    }
+  if (s < 0) return;
+  bool fits = false;
+  dispatch_k(W.K, [&](auto kc) {
+    constexpr int KK = decltype(kc)::value;
+    fits = (W.prec == 64 && !W.split) ? cc_fits<double, KK>() : cc_fits<float, KK>();
+  });
+  if (!fits) return;
+  W.cc_s = s;
+  W.cc_grid = sm_count();
+  W.cc_bar = W.ar.alloc<unsigned>(2);
+  AMG_CUDA(cudaMemset(W.cc_bar, 0, 2 * sizeof(unsigned)));
+  const char* h = std::getenv("AMG_TEST_BARRIER_HANG");
+  W.cc_hang = h && h[0] == '1';
+}
+
 static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false,
                          int variant = 0) {
   long long key = ((long long)variant << 44) | ((long long)split << 40) | ((long long)K << 32) |
@@ -1625,6 +1688,8 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     tune_cache_store(tkey, out);
   }
   if (variant) make_var(P, *W, variant);
+  setup_fused_coarse(P, *W);
+  apply_wait_hook(P, *W);
   P.ws[key] = W;
   return *W;
 }
@@ -1685,6 +1750,62 @@ static void harvest_events(amg_hierarchy* h, std::vector<cudaEvent_t>& pool, boo
 }
 
 // ------------------------------------------------------------ sequences --
+// The levels from W.cc_s down to the coarsest and back up in one cooperative
+// launch (k_coarse_cycle); cur/oth hold each level's iterate and other
+// buffer as the cycle starts.
+template <typename TC>
+static void launch_coarse_cycle(const Plan& P, const Workspace& W, const std::vector<TC*>& cur,
+                                const std::vector<TC*>& oth, const int* done, cudaStream_t st) {
+  CcArgs<TC> a;
+  a.s = W.cc_s;
+  a.L = P.L;
+  a.pre = W.pre;
+  a.post = W.post;
+  for (int k = W.cc_s; k < P.L; ++k) {
+    const Level& Lk = P.lev[k];
+    CcLevel<TC>& c = a.lev[k];
+    c.n = Lk.n;
+    c.rowptr = Lk.rowptr;
+    c.col = Lk.col;
+    c.val = vals<TC>(Lk);
+    c.dinv = k + 1 < P.L ? dinvs<TC>(Lk) : nullptr;
+    c.f = static_cast<TC*>(W.f[k]);
+    c.u = cur[k];
+    c.v = oth[k];
+    if (k + 1 < P.L) {
+      const Transfer& T = P.tr[k];
+      a.tr[k] = CcTransfer<TC>{T.nagg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T)};
+    }
+  }
+  a.cn = P.co.n;
+  a.cnblk = P.co.nblk;
+  a.cblk_off = P.co.blk_off;
+  a.cinv_off = P.co.inv_off;
+  a.cinv = P.co.inv;
+  a.bar_count = W.cc_bar;
+  a.bar_gen = W.cc_bar + 1;
+  a.err = W.err;
+  a.done = done;
+  a.hang_test = W.cc_hang;
+  // about one second at the maximum SM clock; a millisecond under the test hook
+  a.budget = W.cc_hang ? (1ll << 21) : (1ll << 31);
+  dispatch_k(W.K, [&](auto kc) {
+    constexpr int KK = decltype(kc)::value;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)W.cc_grid);
+    cfg.blockDim = dim3(CC_BS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_cycle<TC, KK>, a));
+  });
+  AMG_LAUNCH_CHECK();
+}
+
 template <typename TC>
 static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t st, int mode, const int* done,
                           const KState& ks, std::vector<cudaEvent_t>* pool) {
@@ -1701,7 +1822,9 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   auto F = [&](int k) { return static_cast<TC*>(W.f[k]); };
   // levels >= 1 timed as one span (AMG_KERNEL_COARSE_LEVELS)
   std::unique_ptr<TimedLaunch> coarse_span;
-  for (int k = 0; k + 1 < L; ++k) {
+  // with the fused small-level cycle the restrictions stop at its start level
+  const int kdown = W.cc_s > 0 ? W.cc_s : L - 1;
+  for (int k = 0; k < kdown; ++k) {
     if (k == 1) coarse_span.reset(new TimedLaunch(h, AMG_KERNEL_COARSE_LEVELS, st, pool));
     for (int s = 1; s < W.pre; ++s) {
       launch_smooth<TC>(K, W.nzl[k], P.lev[k], W.rp[k], F(k), cur[k], oth[k], done, st);
@@ -1724,9 +1847,22 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     }
   }
   if (!coarse_span) coarse_span.reset(new TimedLaunch(h, AMG_KERNEL_COARSE_LEVELS, st, pool));
-  launch_coarse<TC>(K, P.co, F(L - 1), cur[L - 1], done, st);
-  TC* res = cur[L - 1];
-  for (int k = L - 2; k >= 0; --k) {
+  TC* res;
+  int kup;
+  if (W.cc_s > 0) {
+    launch_coarse_cycle<TC>(P, W, cur, oth, done, st);
+    // the kernel's out-of-place sweeps: pre - 1 before and post after the
+    // coarse correction on every level it smooths
+    for (int k = W.cc_s; k + 1 < L; ++k)
+      for (int n = 0; n < W.pre - 1 + W.post; ++n) std::swap(cur[k], oth[k]);
+    res = cur[W.cc_s];
+    kup = W.cc_s - 1;
+  } else {
+    launch_coarse<TC>(K, P.co, F(L - 1), cur[L - 1], done, st);
+    res = cur[L - 1];
+    kup = L - 2;
+  }
+  for (int k = kup; k >= 0; --k) {
     if (k == 0) coarse_span.reset();
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_PROLONG_L0 : -1, st, pool);
@@ -2014,6 +2150,7 @@ static void pcg_loop(amg_hierarchy* h, Plan& P, Workspace& W, const amg_opts& o,
   }
   int it = 0, done_iters = 0;
   while (true) {
+    NvtxRange nv_chunk("amg pcg iterations");
     if (o.use_graph) {
       AMG_CUDA(cudaGraphLaunch(W.gexec, st));
       add_launches(W.gkernels);
@@ -2035,6 +2172,18 @@ static void pcg_loop(amg_hierarchy* h, Plan& P, Workspace& W, const amg_opts& o,
   }
 }
 
+// Bounded device waits that gave up (bit 1: a staged copy, bit 2: the grid
+// barrier of the fused small-level cycle): clear the flags and the barrier
+// words, then report AMG_ERR_TIMEOUT.  The context stays usable.
+static void check_waits(Workspace& W, int werr) {
+  if (!werr) return;
+  AMG_CUDA(cudaMemset(W.err, 0, sizeof(int)));
+  if (W.cc_bar) AMG_CUDA(cudaMemset(W.cc_bar, 0, 2 * sizeof(unsigned)));
+  AMG_CUDA(cudaDeviceSynchronize());
+  if (werr & 2) throw Error(AMG_ERR_TIMEOUT, "a bounded wait of the small-level grid barrier gave up");
+  throw Error(AMG_ERR_TIMEOUT, "a bounded wait for a shared-memory staging copy gave up");
+}
+
 // smoother | cycle << 1 for the variant cycles (0: the V-cycle with
 // l1-Jacobi); builds the Gauss-Seidel colouring on first use.
 static int check_variant(amg_hierarchy* owner, Plan& P, const amg_opts& o) {
@@ -2051,6 +2200,7 @@ static int check_variant(amg_hierarchy* owner, Plan& P, const amg_opts& o) {
 
 amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_opts& o, cudaStream_t user,
                    amg_info* info) {
+  NvtxRange nvtx(rq.nsys > 1 ? "amg solve (batched)" : "amg solve");
   int maxr = 0;
   for (int s = 0; s < rq.nsys; ++s) maxr = std::max(maxr, rq.nrhs[s]);
   AMG_REQUIRE(maxr >= 1 && maxr <= 32, "nrhs must be in [1, 32] per call");
@@ -2093,10 +2243,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   int werr = 0;
   AMG_CUDA(cudaMemcpyAsync(&werr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   sj.finish();
-  if (werr) {
-    AMG_CUDA(cudaMemset(W.err, 0, sizeof(int)));
-    throw Error(AMG_ERR_TIMEOUT, "a bounded wait for a shared-memory staging copy gave up");
-  }
+  check_waits(W, werr);
   amg_status res = AMG_OK;
   int idx = 0;
   for (int s = 0; s < rq.nsys; ++s) {
@@ -2119,6 +2266,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
 // z = B r, one V-cycle in the requested precision (caller numbering).
 void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int nrhs, const amg_opts& o,
                 cudaStream_t user) {
+  NvtxRange nv("amg vcycle");
   AMG_REQUIRE(nrhs >= 1 && nrhs <= 32, "nrhs must be in [1, 32]");
   AMG_REQUIRE(o.cycle_precision == 64 || o.cycle_precision == 32, "cycle_precision must be 64 or 32");
   AMG_REQUIRE(o.pre >= 1 && o.post >= 1, "pre and post sweeps must be >= 1");
@@ -2159,11 +2307,15 @@ void run_vcycle(amg_hierarchy* owner, Plan& P, const double* r, double* z, int n
     zout = W.q;
   }
   stage_outputs(P, W, rq, zout, st);
+  int werr = 0;
+  AMG_CUDA(cudaMemcpyAsync(&werr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   sj.finish();
+  check_waits(W, werr);
 }
 
 void run_adjoint_grad(amg_hierarchy* h, const double* lam_caller, const double* x_caller, int nrhs,
                       double* grad, cudaStream_t user) {
+  NvtxRange nv("amg adjoint gradient");
   Plan& P = h->plan;
   const int K = round_k(nrhs);
   Workspace& W = get_ws(P, K, 64, 1, 1);

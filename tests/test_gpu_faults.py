@@ -1,0 +1,77 @@
+"""Failure detection on the GPU without a fault: every device wait of the
+library is bounded, and a wait that gives up turns into AMG_ERR_TIMEOUT on
+the host while the context stays usable.
+
+The test hook AMG_TEST_FIRST_WAIT=1 (read when a solve workspace is
+created) limits the first wait for each staged shared-memory copy to one
+non-blocking poll, which a copy issued a moment earlier cannot meet.  The
+wait after it keeps its full bound, so no copy is left in flight; the solve
+then finishes and reports the timeout.  A hierarchy made without the hook
+afterwards solves normally in the same process.
+"""
+import numpy as np
+import pytest
+
+from paper_1907_04417_gb300.hostsetup import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    from paper_1907_04417_gb300 import amg as A, build
+    build.build()
+    return A
+
+
+def test_staged_copy_wait_gives_up_with_timeout(amg, monkeypatch):
+    import torch
+    P = inputs.anisotropic(128, nrhs=1, levels=4)
+    B = np.random.default_rng(3).uniform(-1, 1, (P.n, 32))
+    Bd = torch.from_numpy(B).cuda()
+    o = amg.opts(cycle_precision=32, maxit=500)
+    monkeypatch.setenv("AMG_TEST_FIRST_WAIT", "1")
+    monkeypatch.setenv("AMG_COARSE_KERNELS", "grouped")   # the grouped levels always stage
+    H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
+    with pytest.raises(amg.AMGError) as e:
+        H.solve(Bd, torch.zeros_like(Bd), o)
+    assert e.value.status == amg.AMG_ERR_TIMEOUT
+    assert "bounded wait" in amg.last_error()
+    H.close()
+    monkeypatch.delenv("AMG_TEST_FIRST_WAIT")
+    monkeypatch.delenv("AMG_COARSE_KERNELS")
+    H2 = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
+    X, infos, st = H2.solve(Bd, torch.zeros_like(Bd), o)
+    assert st == amg.AMG_OK
+    Xc = X.cpu().numpy()
+    rel = np.linalg.norm(B - P.A @ Xc, axis=0) / np.linalg.norm(B, axis=0)
+    assert rel.max() <= 1.1e-8
+    H2.close()
+
+
+def test_grid_barrier_gives_up_with_timeout(amg, monkeypatch):
+    """AMG_TEST_BARRIER_HANG=1 makes the first grid barrier of the fused
+    small-level cycle wait for one CTA more than the grid has: every CTA's
+    bounded wait gives up (about a millisecond), the launch ends, and the
+    solve reports AMG_ERR_TIMEOUT.  A hierarchy made afterwards without the
+    hook solves normally."""
+    import torch
+    P = inputs.anisotropic(128, nrhs=1, levels=4)
+    B = np.random.default_rng(4).uniform(-1, 1, (P.n, 8))
+    Bd = torch.from_numpy(B).cuda()
+    o = amg.opts(cycle_precision=64, maxit=20)
+    monkeypatch.setenv("AMG_TEST_BARRIER_HANG", "1")
+    monkeypatch.setenv("AMG_FUSED_COARSE", "1")
+    H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
+    with pytest.raises(amg.AMGError) as e:
+        H.solve(Bd, torch.zeros_like(Bd), o)
+    assert e.value.status == amg.AMG_ERR_TIMEOUT
+    assert "grid barrier" in amg.last_error()
+    H.close()
+    monkeypatch.delenv("AMG_TEST_BARRIER_HANG")
+    H2 = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
+    X, infos, st = H2.solve(Bd, torch.zeros_like(Bd), amg.opts(cycle_precision=64, maxit=500))
+    assert st == amg.AMG_OK
+    rel = np.linalg.norm(B - P.A @ X.cpu().numpy(), axis=0) / np.linalg.norm(B, axis=0)
+    assert rel.max() <= 1.1e-8
+    H2.close()
