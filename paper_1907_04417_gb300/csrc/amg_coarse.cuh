@@ -10,8 +10,9 @@
 //
 // The barrier spins on a generation word for at most ``budget`` clock64
 // cycles; a CTA whose wait gives up records the error (the host reports
-// AMG_ERR_TIMEOUT) and returns, and every other CTA then gives up at the
-// next barrier, so the launch always ends.  The kernel holds no shared
+// AMG_ERR_TIMEOUT) and returns, every other CTA gives up as soon as it sees
+// the error, and later launches of the solve return at once, so a failed
+// solve costs one bound, not one per cycle.  The kernel holds no shared
 // memory copies in flight and no tensor memory, so a CTA may leave at any
 // barrier.  A test hook (hang_test) makes the first barrier wait for one
 // arrival more than the grid has.
@@ -89,7 +90,8 @@ __device__ __forceinline__ bool cc_barrier(unsigned* count, unsigned* gen, long 
     } else {
       const long long t0 = clock64();
       while (ld_acquire_gpu(gen) == g) {
-        if (clock64() - t0 > budget) {
+        // give up at the bound, or at once when another CTA already gave up
+        if (clock64() - t0 > budget || (ld_acquire_gpu(reinterpret_cast<const unsigned*>(err)) & 2u)) {
           atomicOr(err, 2);
           ok = 0;
           break;
@@ -261,7 +263,8 @@ __device__ __forceinline__ void cc_coarsest(const CcArgs<TC>& a, const TC* __res
 // buffer, and the host replays the same swaps to find level s's result.
 template <typename TC, int K>
 __global__ void __launch_bounds__(CC_BS, 1) k_coarse_cycle(CcArgs<TC> a) {
-  if (*a.done) return;
+  // a barrier of an earlier launch gave up: the solve is already failed
+  if (*a.done || (ld_acquire_gpu(reinterpret_cast<const unsigned*>(a.err)) & 2u)) return;
   bool in_v[CC_MAXL];   // the iterate of level k lives in v (else in u)
 #pragma unroll
   for (int k = 0; k < CC_MAXL; ++k) in_v[k] = false;
