@@ -227,6 +227,12 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
                      cudaStream_t st);
 void build_batch_plan(Plan& out, const std::vector<amg_hierarchy*>& hs, cudaStream_t st);
 
+// device check mode (amg_check.cu): AMG_CHECK=1 or a -DAMG_BOUNDS_CHECK build
+// checks every index array of a built plan on the device and refuses it
+// with AMG_ERR_INVALID_ARG at the first violation
+bool check_mode();
+void check_plan(Plan& P, cudaStream_t st);
+
 // solve (amg_solve.cu)
 struct SolveReq {
   int nsys;

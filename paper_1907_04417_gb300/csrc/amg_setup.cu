@@ -733,6 +733,7 @@ void build_hierarchy(amg_hierarchy* h, const amg_csr* A, int nlev, const int32_t
   P.co.inv = ar.alloc<double>((size_t)C.n * C.n);
   coarsest_inverse(P, C, P.co.inv, st, dflag);
   AMG_CUDA(cudaStreamSynchronize(st));
+  if (check_mode()) check_plan(P, st);
 }
 
 // --------------------------------------------------------------- batches --
@@ -859,6 +860,7 @@ void build_batch_plan(Plan& B, const std::vector<amg_hierarchy*>& hs, cudaStream
     AMG_CUDA(cudaMemcpyAsync(B.perm0 + B.h_sys_row[s], hs[s]->plan.perm0, hs[s]->plan.lev[0].n * 4,
                              cudaMemcpyDeviceToDevice, st));
   AMG_CUDA(cudaStreamSynchronize(st));
+  if (check_mode()) check_plan(B, st);
 }
 
 }  // namespace amg

@@ -77,3 +77,34 @@ def test_grid_barrier_gives_up_with_timeout(amg, monkeypatch):
     rel = np.linalg.norm(B - P.A @ X.cpu().numpy(), axis=0) / np.linalg.norm(B, axis=0)
     assert rel.max() <= 1.1e-8
     H2.close()
+
+
+def test_check_mode_passes_valid_plans(amg, monkeypatch):
+    """AMG_CHECK=1: the device check of every index array passes on a real
+    hierarchy and on a batch plan, and the solves are unchanged."""
+    monkeypatch.setenv("AMG_CHECK", "1")
+    probs = [inputs.anisotropic(N, nrhs=1, levels=4) for N in (48, 64)]
+    Hs = [amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W) for P in probs]
+    X, infos, st = amg.solve_batched(Hs, [P.B for P in probs], options=amg.opts(maxit=500))
+    assert st == amg.AMG_OK
+    for h in Hs:
+        h.close()
+
+
+def test_check_mode_refuses_a_corrupt_column_index(amg, monkeypatch):
+    """A column index planted out of range in level 1 (test hook, after the
+    level is built and before any kernel gathers through it) is found by the
+    check, and setup is refused with the array, level and position named."""
+    P = inputs.anisotropic(48, nrhs=1, levels=4)
+    monkeypatch.setenv("AMG_CHECK", "1")
+    monkeypatch.setenv("AMG_TEST_CORRUPT_COL", "1")
+    with pytest.raises(amg.AMGError) as e:
+        amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    msg = amg.last_error()
+    assert "internal index check" in msg and "level 1" in msg and "col[0]" in msg, msg
+    monkeypatch.delenv("AMG_TEST_CORRUPT_COL")
+    H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)       # the same input without the hook
+    x, info, st = H.solve(P.B[:, :1])
+    assert st == amg.AMG_OK
+    H.close()
