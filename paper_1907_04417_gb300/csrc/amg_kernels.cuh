@@ -1012,6 +1012,14 @@ __global__ void __launch_bounds__(BS) k_smooth_g(int ngrp, const int* __restrict
   const int lane = threadIdx.x & 31, cl = lane % CL, jl = (lane / CL) % JL;
   const int slot = (threadIdx.x >> 5) * SPW + lane / (CL * JL);
   const int ga = blockIdx.x * GROUPS_PER_CTA, gb = min(ga + GROUPS_PER_CTA, ngrp);
+  if (threadIdx.x == 0) {
+    // the CTA's own rows of f, u and D^{-1} (one contiguous range), read
+    // after the gathers: requested into L2 now
+    const int ra0 = __ldg(gstart + ga), ra1 = __ldg(gstart + gb);
+    prefetch_l2(f + (size_t)ra0 * K, (size_t)(ra1 - ra0) * K * sizeof(TC));
+    prefetch_l2(u + (size_t)ra0 * K, (size_t)(ra1 - ra0) * K * sizeof(TC));
+    prefetch_l2(dinv + ra0, (size_t)(ra1 - ra0) * sizeof(TC));
+  }
   const CsrView<TC> cv = group_view<TC>(sg, smraw, __ldg(gstart + ga), __ldg(gstart + gb), rowptr, col, val);
   // every slot runs the same number of passes (the shuffles inside
   // group_acc need the whole warp); a slot without a group adds nothing
@@ -1063,6 +1071,13 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_restrict_g(
   const int a = blockIdx.x;
   const int rs = __ldg(row_start + a), cs = __ldg(coarse_start + a), rc = __ldg(coarse_start + a + 1) - cs;
   const TC* Pa = P + __ldg(blk_start + a);
+  if (threadIdx.x == 0) {
+    // the aggregate's own rows of f and its P block, read after the
+    // gathers: requested into L2 now
+    const int re = __ldg(row_start + a + 1);
+    prefetch_l2(f + (size_t)rs * K, (size_t)(re - rs) * K * sizeof(TC));
+    prefetch_l2(Pa, (size_t)(re - rs) * rc * sizeof(TC));
+  }
   const CsrView<TC> cv = group_view<TC>(sg, smraw, rs, __ldg(row_start + a + 1), rowptr, col, val);
   TC accp[RMAX][CPT];
 #pragma unroll

@@ -49,7 +49,7 @@ def test_timer_changes_nothing_but_time(amg):
 
     X0, it0 = solve()
     t_off = timed()
-    for kid in (amg.KERNEL_SPMV_CG, amg.KERNEL_CG_DIRECTION, amg.KERNEL_COARSE_LEVELS):
+    for kid in (amg.KERNEL_SPMV_CG, amg.KERNEL_CG_UPDATE, amg.KERNEL_COARSE_LEVELS):
         H.timer_enable(kid)
         X1, it1 = solve()
         ms, n = H.timer_read()
