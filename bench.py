@@ -262,18 +262,17 @@ def algorithmic_bytes(kernel, lv, K, mode="df"):
     w = 8 if mode == "f64" else 4            # cycle precision
     rp = 4 * (n + 1)                         # row pointers
     if kernel == "spmv_cg":      # q = A p with p.q
-        if mode == "df":  # A as (hi, lo) floats; z and p_{k-1} gathered, p_k written, x (hi, lo) read
-            # and written (the folded direction update), q (hi, lo) written
-            return nnz * 12 + rp + n * K * (4 + 4 + 4 + 16 + 8)
+        if mode == "df":                     # A as (hi, lo) floats, p float, q (hi, lo)
+            return nnz * 12 + rp + n * K * 4 + n * K * 8
         return nnz * 12 + rp + n * K * 8 + n * K * 8
     if kernel == "cg_update":    # r -= a q with ||r|| (df: x moved to the direction kernel)
         if mode == "df":                     # q (hi, lo) read, r (hi, lo) read and written
             return 3 * n * K * 8
         # x, r read and written, p, q read; u0 = D^-1 r stored; (f32c) f0 = fl32(r)
         return 6 * n * K * 8 + n * 8 + n * K * w + (n * K * 4 if mode == "f32c_f64" else 0)
-    if kernel == "cg_direction":  # p = z + b p
-        if mode == "df":                     # folded into q = A p: no kernel of its own
-            return None
+    if kernel == "cg_direction":  # p = z + b p (df: also x += a p)
+        if mode == "df":                     # z float, p float read/written, x (hi, lo) read/written
+            return n * K * (4 + 8 + 16)
         return n * K * (w + 16)              # z, p float64 read and written
     if kernel == "smooth_l0":    # z = u + D^-1 (f - A u) with r.z
         if mode == "df":                     # f = r_hi; r_lo read for r.z
@@ -299,15 +298,13 @@ KERNEL_IDS = {"spmv_cg": 1, "restrict_l0": 2, "smooth_l0": 3, "prolong_l0": 4, "
 KERNEL_GS_L0 = 6
 
 # q = A p in double-float is bound by float32 arithmetic: per stored non-zero
-# and column the direction p_k = z + beta p_{k-1} at the neighbour (2 float32
-# FMAs) and the multiply-accumulate of a float pair by a float32 (11: exact
-# product 2, low-part product 1, two-sum 6, error accumulation 2); per row and
-# column the row's own p_k (2), the step x += alpha p_{k-1} in double-float
-# (14), the renormalisation (3) and the double-float p.q step (11).  Peak:
-# 152 SMs x 128 float32 lanes x 2.07 GHz (the maximum SM clock) = 40.3e12
-# lane operations per second.
-ALU_OPS_PER_NZ_COL = 13
-ALU_OPS_PER_ROW_COL = 30
+# and column the multiply-accumulate of a float pair by a float32 takes 11
+# float32 operations (exact product 2, low-part product 1, two-sum 6, error
+# accumulation 2); per row and column the renormalisation (3) and the
+# double-float p.q step (11) follow.  Peak: 152 SMs x 128 float32 lanes x
+# 2.07 GHz (the maximum SM clock) = 40.3e12 lane operations per second.
+ALU_OPS_PER_NZ_COL = 11
+ALU_OPS_PER_ROW_COL = 14
 ALU_PEAK_OPS = 152 * 128 * 2.07e9
 
 

@@ -40,49 +40,21 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
   }
 }
 
-// The direction of iteration k at a row, columns lo..lo+CPT-1: p_k = z on
-// the first iteration, else fl32(z + beta p_{k-1}) with beta = bh + bl (the
-// float pair of the float64 beta), rounded in one fixed order, so every
-// CTA that needs p_k at a row forms the same bits.
-template <int CPT>
-__device__ __forceinline__ void dir_at(const float* __restrict__ z, const float* __restrict__ po, unsigned off,
-                                       bool first, const float (&bh)[CPT], const float (&bl)[CPT],
-                                       float (&out)[CPT], float (&pold)[CPT]) {
-  ldv<float, CPT>(z + off, out);
-  if (!first) {
-    ldv<float, CPT>(po + off, pold);
-#pragma unroll
-    for (int t = 0; t < CPT; ++t) out[t] = fmaf(bl[t], pold[t], fmaf(bh[t], pold[t], out[t]));
-  } else {
-#pragma unroll
-    for (int t = 0; t < CPT; ++t) pold[t] = 0.f;
-  }
-}
-
-// One double-float CG step on the float32 pipes, the direction update folded
-// into q = A p.  Iteration k (the device counter *ks.iter):
-//   p_k = z (k = 0) or fl32(z + beta p_{k-1}), formed at every row where it
-//        is needed: each gathered neighbour, and the row itself, whose p_k
-//        is stored for the next iteration (p_k and p_{k-1} alternate between
-//        two buffers by the parity of k);
-//   x += alpha_{k-1} p_{k-1} on the row (the step of the previous iteration;
-//        the last one is applied after the loop by k_cg_x_df);
-//   q = A p_k with A as (val32, vallo) and q stored as a float pair, and p.q
-//        accumulated in double-float; the last CTA forms alpha_k.
-// Rounding p to float32 perturbs the direction at the level of the float32
-// cycle's own rounding; x and r stay consistent because q is formed from the
-// same rounded p.  With one lane group per row the gathers of a batch of
-// rows entries are issued before its first product, and the p.q accumulators
-// live in shared memory, one slot per thread, so that three CTAs fit on an
-// SM.  Offsets into the n x K blocks are 32-bit (n K < 2^32 is checked on
-// the host).
+// q = A p in double-float on the float32 pipes: A as (val32, vallo), p a
+// float32 vector (the search direction is rounded to float32 when it is
+// formed, so every product a_ij p_j is error-free up to the final rounding
+// of the pair); q is stored as a float pair and p.q is accumulated in
+// double-float.  With one lane group per row the gathers of a whole row are
+// issued before its first product (otherwise the loop is software-pipelined
+// one non-zero ahead), and the p.q accumulators live in shared memory, one
+// slot per thread, so that three CTAs fit on an SM.  Offsets into the n x K
+// blocks are 32-bit (n K < 2^32 is checked on the host).
 template <int K, int NZL, bool STG>
 __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
-                                                   const float* __restrict__ alo, const float* __restrict__ z,
-                                                   float* pb0, float* pb1, float* __restrict__ xh,
-                                                   float* __restrict__ xl, float* __restrict__ qh,
-                                                   float* __restrict__ ql, KState ks, Stage sg, int nchunk) {
+                                                   const float* __restrict__ alo, const float* __restrict__ p,
+                                                   float* __restrict__ qh, float* __restrict__ ql, KState ks,
+                                                   Stage sg, int nchunk) {
   if (*ks.done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
@@ -91,20 +63,8 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
   __shared__ float sdot[2 * CPT][BS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
-  const unsigned lo = (unsigned)(cl * CPT);
 #pragma unroll
   for (int t = 0; t < 2 * CPT; ++t) sdot[t][threadIdx.x] = 0.f;
-  // iteration k, its buffers and scalars (alpha_{k-1}, beta_k of the CTA's
-  // system: a persistent launch serves one system)
-  const int itk = *ks.iter;
-  const bool first = itk == 0;
-  const float* po = (itk & 1) ? pb0 : pb1;
-  float* pn = (itk & 1) ? pb1 : pb0;
-  const int sy = (int)gridDim.x == nchunk ? cta_system(ks.sys_cta, ks.nsys) : 0;
-  const double* alpha = ks.alpha + sy * K + lo;   // read per row (registers stay free for the gathers)
-  float bh[CPT], bl[CPT];
-#pragma unroll
-  for (int t = 0; t < CPT; ++t) df_split(ks.beta[sy * K + lo + t], bh[t], bl[t]);
   // row chunks: one per CTA, or (persistent launch) every gridDim.x-th
   // chunk; staged launches take col, val_hi and val_lo (and rowptr) through
   // the double-buffered pipeline, the next chunk arriving while this one is
@@ -136,6 +96,7 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
     va = pv[0];
     vb = pv[1];
   }
+  const unsigned lo = (unsigned)(cl * CPT);
   for (int base = r0 + warp * RPW; base < r1; base += NWARP * RPW) {
     const int i = base + g;
     const bool valid = i < r1;
@@ -145,44 +106,41 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
     if (valid) {
       const int j1 = rp[i + 1 - roff] - joff;
       int j = rp[i - roff] - joff + nzl;
-      if constexpr (NZL == 1 && CPT % 2 == 0) {
-        // predicated batches: every gather of a batch (z and p_{k-1} at U
-        // neighbours) is issued before the first product; the double-float
-        // steps run on column pairs
-        constexpr int U = STG ? 4 : 5, NP = CPT / 2;
-        F2 h2[NP], l2[NP], bh2[NP], bl2[NP];
+      if constexpr (gather_depth<NZL>() != 4 && CPT % 2 == 0) {
+        // predicated batches: every gather of a batch is issued before the
+        // first product (a 9-point row in one memory round trip); the
+        // double-float steps run on column pairs
+        constexpr int U = gather_depth<NZL>(), NP = CPT / 2;
+        F2 h2[NP], l2[NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          h2[q] = l2[q] = F2{0ull};
-          bh2[q] = f2_pack(bh[2 * q], bh[2 * q + 1]);
-          bl2[q] = f2_pack(bl[2 * q], bl[2 * q + 1]);
-        }
-        for (; j < j1; j += U) {
-          F2 zv[U][NP], pv[U][NP];
+        for (int q = 0; q < NP; ++q) h2[q] = l2[q] = F2{0ull};
+        for (; j < j1; j += U * NZL) {
+          F2 xv[U][NP];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const int jj = j + u;
-#pragma unroll
-            for (int q = 0; q < NP; ++q) zv[u][q] = pv[u][q] = F2{0ull};
+            const int jj = j + u * NZL;
             if (jj < j1) {
-              const unsigned off = (unsigned)cc[jj] * (unsigned)K + lo;
+              const float* src = p + (unsigned)cc[jj] * (unsigned)K + lo;
+              if constexpr (NP == 2) {
+                const ulonglong2 t2 = __ldg(reinterpret_cast<const ulonglong2*>(src));
+                xv[u][0] = F2{t2.x};
+                xv[u][1] = F2{t2.y};
+              } else {
 #pragma unroll
-              for (int q = 0; q < NP; ++q) {
-                zv[u][q] = F2{__ldg(reinterpret_cast<const unsigned long long*>(z + off) + q)};
-                if (!first) pv[u][q] = F2{__ldg(reinterpret_cast<const unsigned long long*>(po + off) + q)};
+                for (int q = 0; q < NP; ++q) xv[u][q] = F2{__ldg(reinterpret_cast<const unsigned long long*>(src) + q)};
               }
+            } else {
+#pragma unroll
+              for (int q = 0; q < NP; ++q) xv[u][q] = F2{0ull};
             }
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const int jj = j + u;
+            const int jj = j + u * NZL;
             const float a = jj < j1 ? va[jj] : 0.f, b = jj < j1 ? vb[jj] : 0.f;
             const F2 a2 = f2_pack(a, a), b2 = f2_pack(b, b);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              const F2 x2 = first ? zv[u][q] : f2_fma(bl2[q], pv[u][q], f2_fma(bh2[q], pv[u][q], zv[u][q]));
-              df_acc1_x2(a2, b2, x2, h2[q], l2[q]);
-            }
+            for (int q = 0; q < NP; ++q) df_acc1_x2(a2, b2, xv[u][q], h2[q], l2[q]);
           }
         }
 #pragma unroll
@@ -190,16 +148,46 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
           f2_unpack(h2[q], sh[2 * q], sh[2 * q + 1]);
           f2_unpack(l2[q], sl[2 * q], sl[2 * q + 1]);
         }
-      } else {
-        // scalar columns, or the non-zeros split over NZL lanes: one
-        // neighbour at a time
-        for (; j < j1; j += NZL) {
-          float xv[CPT], pold[CPT];
-          dir_at<CPT>(z, po, (unsigned)cc[j] * (unsigned)K + lo, first, bh, bl, xv, pold);
-          const float a = va[j], b = vb[j];
+      } else if constexpr (gather_depth<NZL>() != 4) {
+        // predicated batches, scalar columns
+        constexpr int U = gather_depth<NZL>();
+        for (; j < j1; j += U * NZL) {
+          float xv[U][CPT];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j + u * NZL;
+            if (jj < j1) {
+              ldv<float, CPT>(p + (unsigned)cc[jj] * (unsigned)K + lo, xv[u]);
+            } else {
+#pragma unroll
+              for (int t = 0; t < CPT; ++t) xv[u][t] = 0.f;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int jj = j + u * NZL;
+            const float a = jj < j1 ? va[jj] : 0.f, b = jj < j1 ? vb[jj] : 0.f;
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[u][t], sh[t], sl[t]);
+          }
+        }
+      } else if (j < j1) {
+        float a = va[j], b = vb[j];
+        float xv[CPT];
+        ldv<float, CPT>(p + (unsigned)cc[j] * (unsigned)K + lo, xv);
+        for (j += NZL; j < j1; j += NZL) {
+          const float a2 = va[j], b2 = vb[j];
+          float yv[CPT];
+          ldv<float, CPT>(p + (unsigned)cc[j] * (unsigned)K + lo, yv);
 #pragma unroll
           for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[t], sh[t], sl[t]);
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) xv[t] = yv[t];
+          a = a2;
+          b = b2;
         }
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[t], sh[t], sl[t]);
       }
 #pragma unroll
       for (int t = 0; t < CPT; ++t) df_norm(sh[t], sl[t]);
@@ -214,26 +202,9 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
         }
     }
     if (valid && nzl == 0) {
-      // the row's own p_k (stored for the next iteration) and the step of
-      // the previous iteration, x += alpha_{k-1} p_{k-1}
       const unsigned o = (unsigned)i * (unsigned)K + lo;
-      float pv[CPT], pold[CPT];
-      dir_at<CPT>(z, po, o, first, bh, bl, pv, pold);
-      stv<float, CPT>(pn + o, pv);
-      if (!first) {
-        float xa[CPT], xb[CPT];
-        ldv<float, CPT>(xh + o, xa);
-        ldv<float, CPT>(xl + o, xb);
-#pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-          float ah, al;
-          df_split(alpha[t], ah, al);
-          df_acc1(ah, al, pold[t], xa[t], xb[t]);
-          df_norm(xa[t], xb[t]);
-        }
-        stv<float, CPT>(xh + o, xa);
-        stv<float, CPT>(xl + o, xb);
-      }
+      float pv[CPT];
+      ldv<float, CPT>(p + o, pv);
       stv<float, CPT>(qh + o, sh);
       stv<float, CPT>(ql + o, sl);
 #pragma unroll
@@ -364,7 +335,7 @@ __global__ void __launch_bounds__(BS) k_cg_init(const int* __restrict__ cta_row,
 }
 
 // p = z + beta p in float64 (the float64 CG; the double-float CG has
-// k_cg_q_df).  z is stored in the cycle precision TZ; ``first`` starts the recurrence
+// k_cg_p_df).  z is stored in the cycle precision TZ; ``first`` starts the recurrence
 // (p = z, the previous p is not read).
 template <int K, typename TZ>
 __global__ void __launch_bounds__(BS) k_cg_p(const int* __restrict__ cta_row, const TZ* __restrict__ z,
@@ -401,7 +372,7 @@ __device__ __forceinline__ void split2(double v, float& h, float& l) { df_split(
 
 // r -= alpha q, ||r||^2; u0 = D^{-1} r_hi (the first pre-sweep from zero;
 // not stored when u0 is null, the cycle then folding it into A D^{-1}).
-// (x is advanced inside k_cg_q_df, which gathers p anyway.)
+// (x is advanced by k_cg_p_df, which streams p anyway.)
 template <int K>
 __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta_row, float* __restrict__ rh,
                                                      float* __restrict__ rl, const float* __restrict__ qh,
@@ -447,6 +418,54 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
   cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
   if (!arrive_two_level(ks, RED_UPDATE, K, sm, tot)) return;
   finish_update<K>(ks, sm, tot);
+}
+
+// x += alpha p (with the alpha of this iteration, x a double-float pair and
+// p an exact float32), then p = fl32(z + beta p); ``first`` starts the
+// recurrence (p = z, x untouched).  Rounding the search direction to float32
+// only perturbs it at the level of the float32 cycle's own rounding: x and r
+// stay consistent because q = A p is formed from the same rounded p.  After
+// the last iteration k_cg_x_df applies the final alpha p, which this kernel
+// skips once every column has stopped.
+template <int K>
+__global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
+                                                float* __restrict__ p, float* __restrict__ xh,
+                                                float* __restrict__ xl, KState ks, int first, int nchunk) {
+  if (*ks.done) return;
+  constexpr int CPT = VT<float, K>::CPT;
+  const int cfirst = (int)((threadIdx.x * CPT) % K);
+  const int s = cta_system(ks.sys_cta, ks.nsys);
+  float bh[CPT], bl[CPT], ah[CPT], al[CPT];
+#pragma unroll
+  for (int t = 0; t < CPT; ++t) {
+    split2(ks.beta[s * K + cfirst + t], bh[t], bl[t]);
+    split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+  }
+  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+  const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
+  for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
+    float zv[CPT], pv[CPT];
+    ldv<float, CPT>(z + e, zv);
+    if (first) {
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) pv[t] = zv[t];
+    } else {
+      float xa[CPT], xb[CPT];
+      ldp<float, CPT>(p + e, pv);
+      ldp<float, CPT>(xh + e, xa);
+      ldp<float, CPT>(xl + e, xb);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
+        df_norm(xa[t], xb[t]);
+        pv[t] = fmaf(bl[t], pv[t], fmaf(bh[t], pv[t], zv[t]));
+      }
+      stv<float, CPT>(xh + e, xa);
+      stv<float, CPT>(xl + e, xb);
+    }
+    stv<float, CPT>(p + e, pv);
+  }
+  }
 }
 
 // x += alpha p once after the loop (the step of the last iteration; the
@@ -577,8 +596,7 @@ struct Workspace {
   bool split = false;  // double-float CG vectors (float32-cycle mode)
   bool u0free = false; // split with one pre-sweep: u0 = D^{-1} r_hi is folded into A D^{-1} (never stored)
   float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr;
-  float *ph = nullptr, *ph2 = nullptr;  // p_k in ph (k even) or ph2 (k odd); float32 (see k_cg_q_df)
-  float *qh = nullptr, *ql = nullptr;
+  float *ph = nullptr, *qh = nullptr, *ql = nullptr;  // p is float32 (see k_cg_p_df)
   std::vector<void*> f, u, v;
   KState ks{};
   int* zero_flag = nullptr;
@@ -1342,7 +1360,12 @@ static void tune_persist(Plan& P, Workspace& W) {
     launch_update_df(W, P.lev[0], 0);
     W.ks = keep;
   });
-  W.p_grid = 0;   // the direction update runs inside q = A p (k_cg_q_df)
+  pick("p", W.p_grid, false, [&] {
+    KState keep = W.ks;
+    W.ks.done = tdone;
+    launch_cg_p(P, W, P.lev[0], 0, 0);
+    W.ks = keep;
+  });
   // post-smoother: persistent grids unstaged (code grid) and staged (code -grid)
   int post_code = 0;
   {
@@ -1560,11 +1583,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   W->u0free = split && pre == 1 && P.L > 1;
   if (W->u0free) ensure_scaled(P);
   if (split) {
-    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->ph2, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
-    // the direction buffers hold finite values from the start (the last step
-    // x += alpha p reads one of them even when no iteration ran)
-    AMG_CUDA(cudaMemset(W->ph, 0, n0k * sizeof(float)));
-    AMG_CUDA(cudaMemset(W->ph2, 0, n0k * sizeof(float)));
+    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
   } else {
     W->p = ar.alloc<double>(n0k);
   }
@@ -1638,7 +1657,6 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   ks.active = ar.alloc<int>(P.nsys);
   ks.done = ar.alloc<int>(1);
   ks.iter = ar.alloc<int>(1);
-  AMG_CUDA(cudaMemset(ks.iter, 0, sizeof(int)));
   ks.sys_cta = r0p.sys_cta;
   ks.nsys = P.nsys;
   AMG_CUDA(cudaMemset(ks.done, 0, sizeof(int)));
@@ -1881,8 +1899,7 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
           size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
           ensure_smem(kern, smem);
           const int grid = W.q_grid > 0 ? W.q_grid : W.rq.ncta;
-          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo,
-                                       reinterpret_cast<const float*>(W.z), W.ph, W.ph2, W.xh, W.xl, W.qh, W.ql,
+          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.qh, W.ql,
                                        W.ksq, sg, W.rq.ncta);
         }
       });
@@ -1929,7 +1946,8 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     if (W.split)
-      throw Error(AMG_ERR_INVALID_ARG, "internal: the double-float direction update runs inside q = A p");
+      k_cg_p_df<KK><<<W.p_grid ? W.p_grid : W.rp[0].ncta, BS, 0, st>>>(
+          W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph, W.xh, W.xl, W.ks, first, W.rp[0].ncta);
     else if (z_is_f32(P, W))
       k_cg_p<KK, float><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.p,
                                                      W.ks, first);
@@ -1987,8 +2005,7 @@ static void enqueue_start(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     if (!W.u0free) launch_presmooth0<TC>(W.K, L0, W.rp[0], W.r, static_cast<TC*>(W.u[0]), f0, W.ks.done, st);
     enqueue_cycle<TC>(h, P, W, st, 0, W.ks.done, W.ks, nullptr);
   }
-  // the double-float CG forms p_0 = z inside its first q = A p
-  if (!W.split) launch_cg_p(P, W, L0, 1, st);
+  launch_cg_p(P, W, L0, 1, st);
 }
 
 template <typename TC>
@@ -2013,7 +2030,6 @@ static void enqueue_iteration(amg_hierarchy* h, Plan& P, Workspace& W, cudaStrea
     enqueue_cycle<TC>(h, P, W, st, 1, W.ks.done, W.ks, pool);
     if (P.L == 1) launch_rz(W, L0, 1, st);
   }
-  if (W.split) return;  // p = z + beta p is folded into the next q = A p
   TimedLaunch tl(h, AMG_KERNEL_CG_DIRECTION, st, pool);
   launch_cg_p(P, W, L0, 0, st);
 }
@@ -2209,9 +2225,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   if (W.split) {
     dispatch_k(K, [&](auto kc) {
       constexpr int KK = decltype(kc)::value;
-      // the last step x += alpha_k p_k: p_k of the last iteration k = iter - 1
-      const float* plast = ((*W.h_iter - 1) & 1) ? W.ph2 : W.ph;
-      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, plast, W.xh, W.xl, W.ks);
+      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.ph, W.xh, W.xl, W.ks);
     });
     AMG_LAUNCH_CHECK();
     launch_pair(false, (long long)W.n0 * K, nullptr, W.xh, W.xl, W.x, nullptr, st);

@@ -54,13 +54,12 @@ def test_roofline_counts_double_float_mode():
     """The float32 cycle with double-float CG: what each level-0 kernel reads
     and writes once (the first pre-sweep folded into the scaled matrix)."""
     ab = lambda k: bench.algorithmic_bytes(k, LV, K, "df")  # noqa: E731
-    # col + (hi, lo) values, rowptr; z and p_{k-1} gathered, p_k written, x (hi, lo) read and
-    # written (the direction update folded in), q (hi, lo) written
-    assert ab("spmv_cg") == nnz * 12 + rp + n * K * 36
+    # col + (hi, lo) values, rowptr, p float read, q (hi, lo) written
+    assert ab("spmv_cg") == nnz * 12 + rp + n * K * 4 + n * K * 8
     # q (hi, lo) read, r (hi, lo) read and written
     assert ab("cg_update") == 3 * n * K * 8
-    # no direction kernel of its own
-    assert ab("cg_direction") is None
+    # z read, p read and written, x (hi, lo) read and written
+    assert ab("cg_direction") == n * K * 28
     # col + float values, rowptr, D^-1, f = r_hi, u, r_lo read, z written
     assert ab("smooth_l0") == nnz * 8 + rp + n * 4 + 4 * n * K * 4
     # scaled matrix, f read once, P, fc and uc written, D_c^-1 read
@@ -68,7 +67,7 @@ def test_roofline_counts_double_float_mode():
     # P, uc read, f read, u written, D^-1 read
     assert ab("prolong_l0") == npv * 4 + n1 * K * 4 + 2 * n * K * 4 + n * 4
     assert ab("coarse_levels") is None
-    assert bench.alu_ops("spmv_cg", LV, K) == 9000 * K * 13 + 1000 * K * 30
+    assert bench.alu_ops("spmv_cg", LV, K) == 9000 * K * 11 + 1000 * K * 14
     assert bench.alu_ops("restrict_l0", LV, K) is None
     assert bench.ALU_PEAK_OPS == pytest.approx(152 * 128 * 2.07e9)
 
