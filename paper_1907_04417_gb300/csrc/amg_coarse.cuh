@@ -105,33 +105,38 @@ __device__ __forceinline__ bool cc_barrier(unsigned* count, unsigned* gen, long 
   return ok != 0;
 }
 
-// Thread-level work items: (row, CPT-wide column chunk).
+// Work items: (row, CPT-wide column chunk), NCH chunks per row.
 template <typename TC, int K>
 struct CcItems {
   static constexpr int CPT = VT<TC, K>::CPT, NCH = K / CPT;
+  // lanes of one warp-row in cc_sweep: NCH column chunks x NZL slices of the row
+  static constexpr int NZL = 32 / NCH;
 };
 
-// y = f - A x on a level (out-of-place), or, with dinv, y = x + D^{-1} (f - A x)
+__device__ __forceinline__ long long cc_warp() { return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ long long cc_warps() { return ((long long)gridDim.x * blockDim.x) >> 5; }
+
+// y = f - A x on a level (out-of-place), or, with smooth, y = x + D^{-1} (f - A x).
+// One warp per row: lane = (slice, chunk); the NZL slices take every NZL-th
+// non-zero, four gathers in flight each, and are combined by shuffles.
 template <typename TC, int K>
 __device__ __forceinline__ void cc_sweep(const CcLevel<TC>& L, const TC* __restrict__ x, TC* __restrict__ y,
                                          bool smooth) {
-  constexpr int CPT = CcItems<TC, K>::CPT, NCH = CcItems<TC, K>::NCH;
-  const long long items = (long long)L.n * NCH;
-  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-       it += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(it / NCH), c0 = (int)(it % NCH) * CPT;
+  constexpr int CPT = CcItems<TC, K>::CPT, NCH = CcItems<TC, K>::NCH, NZL = CcItems<TC, K>::NZL;
+  const int lane = threadIdx.x & 31, ch = lane % NCH, sl = lane / NCH, c0 = ch * CPT;
+  for (long long i = cc_warp(); i < L.n; i += cc_warps()) {
     TC acc[CPT];
 #pragma unroll
     for (int t = 0; t < CPT; ++t) acc[t] = TC(0);
-    const int j0 = L.rowptr[i], j1 = L.rowptr[i + 1];
-    int j = j0;
-    for (; j + 3 < j1; j += 4) {
+    const int j1 = L.rowptr[i + 1];
+    int j = L.rowptr[i] + sl;
+    for (; j + 3 * NZL < j1; j += 4 * NZL) {
       int c[4];
       TC a[4], xv[4][CPT];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        c[q] = L.col[j + q];
-        a[q] = L.val[j + q];
+        c[q] = L.col[j + q * NZL];
+        a[q] = L.val[j + q * NZL];
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) ldp<TC, CPT>(x + (size_t)c[q] * K + c0, xv[q]);
@@ -140,26 +145,32 @@ __device__ __forceinline__ void cc_sweep(const CcLevel<TC>& L, const TC* __restr
 #pragma unroll
         for (int t = 0; t < CPT; ++t) acc[t] = fma(a[q], xv[q][t], acc[t]);
     }
-    for (; j < j1; ++j) {
+    for (; j < j1; j += NZL) {
       TC xv[CPT];
       ldp<TC, CPT>(x + (size_t)L.col[j] * K + c0, xv);
       const TC a = L.val[j];
 #pragma unroll
       for (int t = 0; t < CPT; ++t) acc[t] = fma(a, xv[t], acc[t]);
     }
-    TC fv[CPT], out[CPT];
-    ldp<TC, CPT>(L.f + (size_t)i * K + c0, fv);
-    if (smooth) {
-      TC xi[CPT];
-      ldp<TC, CPT>(x + (size_t)i * K + c0, xi);
-      const TC di = L.dinv[i];
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[t], xi[t]);
-    } else {
+    for (int off = NCH; off < 32; off <<= 1)
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) out[t] = fv[t] - acc[t];
+      for (int t = 0; t < CPT; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], off);
+    if (sl == 0) {
+      TC fv[CPT], out[CPT];
+      ldp<TC, CPT>(L.f + (size_t)i * K + c0, fv);
+      if (smooth) {
+        TC xi[CPT];
+        ldp<TC, CPT>(x + (size_t)i * K + c0, xi);
+        const TC di = L.dinv[i];
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) out[t] = fma(di, fv[t] - acc[t], xi[t]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) out[t] = fv[t] - acc[t];
+      }
+      stv<TC, CPT>(y + (size_t)i * K + c0, out);
     }
-    stv<TC, CPT>(y + (size_t)i * K + c0, out);
   }
 }
 
@@ -173,14 +184,16 @@ __device__ __forceinline__ int cc_find(const int* __restrict__ start, int n, int
   return lo;
 }
 
-// fc = P^T t; uc = D_c^{-1} fc when the coarse level is smoothed
+// fc = P^T t; uc = D_c^{-1} fc when the coarse level is smoothed.  One warp
+// per (coarse dof, column chunk): the lanes take the aggregate's rows in
+// turn and their partial sums are combined by shuffles.
 template <typename TC, int K>
 __device__ __forceinline__ void cc_restrict(const CcTransfer<TC>& T, const TC* __restrict__ t,
                                             const CcLevel<TC>& C, bool smooth_next) {
   constexpr int CPT = CcItems<TC, K>::CPT, NCH = CcItems<TC, K>::NCH;
+  const int lane = threadIdx.x & 31;
   const long long items = (long long)C.n * NCH;
-  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-       it += (long long)gridDim.x * blockDim.x) {
+  for (long long it = cc_warp(); it < items; it += cc_warps()) {
     const int cd = (int)(it / NCH), c0 = (int)(it % NCH) * CPT;
     const int a = cc_find(T.coarse_start, T.nagg, cd);
     const int cs = T.coarse_start[a], ra = T.coarse_start[a + 1] - cs, p = cd - cs;
@@ -189,19 +202,25 @@ __device__ __forceinline__ void cc_restrict(const CcTransfer<TC>& T, const TC* _
     TC acc[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) acc[q] = TC(0);
-    for (int i = rs; i < re; ++i) {
+    for (int i = rs + lane; i < re; i += 32) {
       TC tv[CPT];
       ldp<TC, CPT>(t + (size_t)i * K + c0, tv);
       const TC pv = Pa[(size_t)(i - rs) * ra];
 #pragma unroll
       for (int q = 0; q < CPT; ++q) acc[q] = fma(pv, tv[q], acc[q]);
     }
-    stv<TC, CPT>(C.f + (size_t)cd * K + c0, acc);
-    if (smooth_next) {
-      const TC d = C.dinv[cd];
 #pragma unroll
-      for (int q = 0; q < CPT; ++q) acc[q] *= d;
-      stv<TC, CPT>(C.u + (size_t)cd * K + c0, acc);
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if (lane == 0) {
+      stv<TC, CPT>(C.f + (size_t)cd * K + c0, acc);
+      if (smooth_next) {
+        const TC d = C.dinv[cd];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) acc[q] *= d;
+        stv<TC, CPT>(C.u + (size_t)cd * K + c0, acc);
+      }
     }
   }
 }
@@ -235,25 +254,29 @@ __device__ __forceinline__ void cc_prolong(const CcTransfer<TC>& T, const TC* __
   }
 }
 
-// u = A_c^{-1} f with the float64 inverse of each diagonal block
+// u = A_c^{-1} f with the float64 inverse of each diagonal block.  One warp
+// per row: lane = (column, slice), C = min(K, 32) columns and 32 / C slices
+// of the inner index, combined by shuffles.
 template <typename TC, int K>
 __device__ __forceinline__ void cc_coarsest(const CcArgs<TC>& a, const TC* __restrict__ f, TC* __restrict__ u) {
-  const long long items = (long long)a.cn * K;
-  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-       it += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(it / K), c = (int)(it % K);
-    const int b = cc_find(a.cblk_off, a.cnblk, row);
+  constexpr int C = K < 32 ? K : 32, JP = 32 / C;
+  const int lane = threadIdx.x & 31, c = lane % C, jp = lane / C;
+  for (long long row = cc_warp(); row < a.cn; row += cc_warps()) {
+    const int b = cc_find(a.cblk_off, a.cnblk, (int)row);
     const int b0 = a.cblk_off[b], nb = a.cblk_off[b + 1] - b0;
     const double* Ar = a.cinv + a.cinv_off[b] + (size_t)(row - b0) * nb;
     const TC* fc = f + (size_t)b0 * K + c;
     double s0 = 0.0, s1 = 0.0;
-    int j = 0;
-    for (; j + 1 < nb; j += 2) {
+    int j = jp;
+    for (; j + JP < nb; j += 2 * JP) {
       s0 = fma(Ar[j], (double)fc[(size_t)j * K], s0);
-      s1 = fma(Ar[j + 1], (double)fc[(size_t)(j + 1) * K], s1);
+      s1 = fma(Ar[j + JP], (double)fc[(size_t)(j + JP) * K], s1);
     }
     if (j < nb) s0 = fma(Ar[j], (double)fc[(size_t)j * K], s0);
-    u[(size_t)row * K + c] = (TC)(s0 + s1);
+    double sv = s0 + s1;
+#pragma unroll
+    for (int off = C; off < 32; off <<= 1) sv += __shfl_xor_sync(0xffffffffu, sv, off);
+    if (jp == 0) u[(size_t)row * K + c] = (TC)sv;
   }
 }
 

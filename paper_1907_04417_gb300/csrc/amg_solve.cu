@@ -1522,10 +1522,14 @@ static void apply_wait_hook(Plan& P, Workspace& W) {
   for (auto& t : P.tr) set(t.gsg);
 }
 
-// Start level of the fused small-level cycle: the first level k >= 1 above
-// the coarsest whose sweep is at most 2^25 multiply-adds (nnz_k K), if the
-// cooperative launch fits one CTA per SM.  AMG_FUSED_COARSE=0 keeps the
-// launch-per-step cycle; AMG_TEST_BARRIER_HANG=1 is the barrier test hook.
+// Start level of the fused small-level cycle (W.cc_s, -1: off).  Eligible
+// starts: levels 1 <= s <= L-2 with at most 2^21 (row, column) items, if the
+// cooperative launch fits one CTA per SM.  Tuned workspaces time one
+// graph-captured V-cycle with the fused cycle off and from each eligible
+// start and keep the fastest (the choice joins the tuning cache); others
+// take the first eligible level with at most 2^19 items.
+// AMG_FUSED_COARSE=0 keeps the launch-per-step cycle, =1 forces the first
+// eligible start; AMG_TEST_BARRIER_HANG=1 is the barrier test hook.
 template <typename TC, int K>
 static bool cc_fits() {
   int nb = 0;
@@ -1535,29 +1539,52 @@ static bool cc_fits() {
   }
   return nb >= 1;
 }
-static void setup_fused_coarse(Plan& P, Workspace& W) {
+static float time_vcycle_graph(Plan& P, Workspace& W);
+static void setup_fused_coarse(Plan& P, Workspace& W, bool autotune, int cached_s) {
   W.cc_s = -1;
   const char* e = std::getenv("AMG_FUSED_COARSE");
   if ((e && e[0] == '0') || P.L < 3 || P.L > CC_MAXL || W.variant) return;
-  int s = -1;
+  std::vector<int> starts;
   for (int k = 1; k + 1 < P.L; ++k)
-    if ((double)P.lev[k].nnz * W.K <= (double)(1 << 25)) {
-      s = k;
-      break;
-    }
-  if (s < 0) return;
+    if ((double)P.lev[k].n * W.K <= (double)(1 << 21)) starts.push_back(k);
+  if (starts.empty()) return;
   bool fits = false;
   dispatch_k(W.K, [&](auto kc) {
     constexpr int KK = decltype(kc)::value;
     fits = (W.prec == 64 && !W.split) ? cc_fits<double, KK>() : cc_fits<float, KK>();
   });
   if (!fits) return;
-  W.cc_s = s;
   W.cc_grid = sm_count();
   W.cc_bar = W.ar.alloc<unsigned>(2);
   AMG_CUDA(cudaMemset(W.cc_bar, 0, 2 * sizeof(unsigned)));
   const char* h = std::getenv("AMG_TEST_BARRIER_HANG");
   W.cc_hang = h && h[0] == '1';
+  if ((e && e[0] == '1') || W.cc_hang) {
+    W.cc_s = starts[0];
+  } else if (cached_s >= -1) {
+    W.cc_s = std::find(starts.begin(), starts.end(), cached_s) != starts.end() ? cached_s : -1;
+  } else if (autotune) {
+    W.cc_s = -1;
+    float best = time_vcycle_graph(P, W);
+    if (tune_log()) fprintf(stderr, "[tune] V-cycle, launch per step: %.1f us\n", best * 1e3);
+    int bs = -1;
+    for (int s : starts) {
+      W.cc_s = s;
+      const float ms = time_vcycle_graph(P, W);
+      if (tune_log()) fprintf(stderr, "[tune] V-cycle, fused small levels from %d: %.1f us\n", s, ms * 1e3);
+      if (ms < best) {
+        best = ms;
+        bs = s;
+      }
+    }
+    W.cc_s = bs;
+  } else {
+    for (int s : starts)
+      if ((double)P.lev[s].n * W.K <= (double)(1 << 19)) {
+        W.cc_s = s;
+        break;
+      }
+  }
 }
 
 static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split = false, bool autotune = false,
@@ -1623,7 +1650,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   // cached choices: per smoothed level 3, per transfer 3, q 4, persistent 4
   const std::string tkey = tune_key(P, K, prec, pre, post, split);
   std::vector<long long> tv;
-  const bool cached = autotune && tune_cache_load(tkey, tv) && tv.size() == (size_t)(6 * nt + 8);
+  const bool cached = autotune && tune_cache_load(tkey, tv) && tv.size() == (size_t)(6 * nt + 9);
   if (cached) {
     for (int k = 0; k < nt; ++k) apply_level(P, *W, k, tv[3 * k], (int)tv[3 * k + 1], (int)tv[3 * k + 2]);
   } else if (autotune) {
@@ -1673,22 +1700,26 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     if (t[0] > 0 || t[1] > 0) apply_q(P, *W, t[0], (int)t[1], (int)t[2], (int)t[3]);
     t += 4;
     if (split && P.nsys == 1) apply_persist(*W, (int)t[0], (int)t[1], (int)t[2]);
-  } else if (autotune) {
+  }
+  std::vector<long long> out;
+  if (!cached && autotune) {
     for (int k = 0; k + 1 < P.L; ++k) {
       if (prec == 64) tune_transfer<double>(P, *W, k);
       else tune_transfer<float>(P, *W, k);
     }
     tune_q(P, *W);
     if (split && P.nsys == 1) tune_persist(P, *W);
-    std::vector<long long> out;
     for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_rp[k], W->t_rps[k], W->t_nzl[k]});
     for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_tp[k], W->t_tps[k], W->t_tpw[k]});
     out.insert(out.end(), {W->t_q, W->t_qn, W->t_qs, W->t_qg});
     out.insert(out.end(), {(long long)W->t_pu, (long long)W->t_pp, (long long)W->t_ppost, 0LL});
-    tune_cache_store(tkey, out);
   }
   if (variant) make_var(P, *W, variant);
-  setup_fused_coarse(P, *W);
+  setup_fused_coarse(P, *W, autotune, cached ? (int)tv[6 * nt + 8] : -2);
+  if (autotune && !cached) {
+    out.push_back(W->cc_s);
+    tune_cache_store(tkey, out);
+  }
   apply_wait_hook(P, *W);
   P.ws[key] = W;
   return *W;
@@ -1884,6 +1915,53 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   if (pers && !W.post_stage) rp0.sg.enabled = 0;
   launch_post0<TC>(K, W.nzl[0], P.lev[0], rp0, F(0), cur[0], W.r, W.split ? W.rl : nullptr,
                    reinterpret_cast<TC*>(W.z), pers ? W.ksf_post : ks, mode, st, pers ? W.post_grid : 0);
+}
+
+// Device time of one V-cycle (mode 2: no CG scalars) replayed from a CUDA
+// graph, the minimum of five replays; the fused small-level cycle's tuner.
+static float time_vcycle_graph(Plan& P, Workspace& W) {
+  cudaStream_t st;
+  AMG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  AMG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  try {
+    if (W.prec == 64 && !W.split) enqueue_cycle<double>(nullptr, P, W, st, 2, W.zero_flag, W.ks, nullptr);
+    else enqueue_cycle<float>(nullptr, P, W, st, 2, W.zero_flag, W.ks, nullptr);
+  } catch (...) {
+    g_capturing = false;
+    cudaStreamEndCapture(st, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(st);
+    throw;
+  }
+  g_capturing = false;
+  AMG_CUDA(cudaStreamEndCapture(st, &g));
+  AMG_CUDA(cudaGraphInstantiate(&ge, g, 0));
+  cudaEvent_t e0, e1;
+  AMG_CUDA(cudaEventCreate(&e0));
+  AMG_CUDA(cudaEventCreate(&e1));
+  AMG_CUDA(cudaGraphLaunch(ge, st));
+  float best = 1e30f;
+  for (int r = 0; r < 5; ++r) {
+    AMG_CUDA(cudaEventRecord(e0, st));
+    AMG_CUDA(cudaGraphLaunch(ge, st));
+    AMG_CUDA(cudaEventRecord(e1, st));
+    AMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, ms);
+  }
+  int werr = 0;
+  AMG_CUDA(cudaMemcpy(&werr, W.err, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(st);
+  AMG_REQUIRE(werr == 0, "internal: a bounded wait gave up while timing the V-cycle");
+  return best;
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {

@@ -57,8 +57,9 @@ def test_fused_small_levels_match_oracle(amg, case, monkeypatch, prec, tol, ncol
 
 def test_fused_batch_of_uneven_systems(amg, monkeypatch):
     """The batched plan (block-diagonal levels and coarsest inverse) through
-    the fused cycle: every column reaches the true residual."""
-    monkeypatch.delenv("AMG_FUSED_COARSE", raising=False)
+    the fused cycle (forced, AMG_FUSED_COARSE=1): every column reaches the
+    true residual."""
+    monkeypatch.setenv("AMG_FUSED_COARSE", "1")   # the fused path, not the tuner's choice
     probs = [inputs.anisotropic(N, nrhs=1, levels=4, cfg=2) for N in (64, 96)]
     Hs = [amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W) for P in probs]
     Bs = [np.random.default_rng(s).uniform(-1, 1, (P.n, 3)) for s, P in enumerate(probs)]
