@@ -7,7 +7,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
-#include <string>
 
 #include "amg_coarse.cuh"
 #include "amg_launch.cuh"
@@ -1153,11 +1152,7 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
   // the tiled restriction: CTA ranges whose rows of u are staged in shared
   // memory (one bulk copy), one warp per aggregate
   bool tile_best = false;
-  // AMG_RESTRICT_KERNEL=tile takes the tiled restriction wherever it fits
-  const char* rk = std::getenv("AMG_RESTRICT_KERNEL");
-  const bool force_tile = rk && std::string(rk) == "tile";
-  if (force_tile) best = 1e30f;
-  if (!grp_best || force_tile) {
+  if (!grp_best) {
     Arena tmp3;
     for (int t : {128, 256, 512, 1024}) {
       TPart tt = make_tpart(tmp3, P.tr[k], P.lev[k], K, W.err, t);
@@ -1172,7 +1167,6 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
         bt = t;
         bs = 0;
         tile_best = true;
-        grp_best = false;
       }
     }
     AMG_CUDA(cudaDeviceSynchronize());

@@ -71,35 +71,3 @@ def test_fused_batch_of_uneven_systems(amg, monkeypatch):
             assert rel.max() <= 1.1e-8
     for h in Hs:
         h.close()
-
-
-@pytest.mark.parametrize("prec", [64, 32])
-def test_tiled_restriction_against_oracle(amg, case, monkeypatch, prec):
-    """The tiled restriction (AMG_RESTRICT_KERNEL=tile forces it on every
-    level where it fits) inside tuned 32-column solves: the float64 iterate
-    at a fixed iteration count against the oracle's, and the float32-cycle
-    solve to the true residual within three iterations of float64."""
-    import torch
-    P, Ho = case
-    monkeypatch.setenv("AMG_RESTRICT_KERNEL", "tile")
-    monkeypatch.setenv("AMG_FUSED_COARSE", "0")
-    H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
-    B = np.random.default_rng(31).uniform(-1, 1, (P.n, 32))
-    B[:, 0] = P.B[:, 0]
-    Bd = torch.from_numpy(B).cuda()
-    if prec == 64:
-        X, info, st = H.solve(Bd, options=amg.opts(cycle_precision=64, maxit=15))
-        assert st == amg.AMG_ERR_NOT_CONVERGED and info[0]["iters"] == 15
-        xo, _ = O.solve(Ho, P.B[:, 0], fixed_iters=15)
-        err = np.linalg.norm(X[:, 0].cpu().numpy() - xo) / np.linalg.norm(xo)
-        assert err <= 1e-10, err
-    else:
-        X64, i64, _ = H.solve(Bd, options=amg.opts(cycle_precision=64, maxit=2000))
-        X32, i32, st = H.solve(Bd, options=amg.opts(cycle_precision=32, maxit=2000))
-        assert st == amg.AMG_OK
-        Xc = X32.cpu().numpy()
-        rel = np.linalg.norm(B - P.A @ Xc, axis=0) / np.linalg.norm(B, axis=0)
-        assert rel.max() <= 1.1e-8
-        for c in range(32):
-            assert i32[c]["iters"] <= i64[c]["iters"] + 3
-    H.close()
