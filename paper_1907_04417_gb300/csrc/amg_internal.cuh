@@ -146,7 +146,6 @@ struct TPart {
   int warp = 0;    // restriction: 0 CTA ranges, 1 one warp per aggregate (3: staged), 2 grouped (one CTA per aggregate)
   int pwarp = 0;   // prolongation by one warp per aggregate (no CTA ranges)
   int jl = 1;      // grouped restriction: lanes splitting a group's pattern columns
-  int tile = 0;    // restriction from a shared-memory tile of u over the CTA ranges (k_restrict_t)
   Stage wsg;       // staging of the warp-per-aggregate restriction (NWARP aggregates per CTA)
 };
 

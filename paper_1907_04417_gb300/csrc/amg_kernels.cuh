@@ -940,138 +940,6 @@ __global__ void __launch_bounds__(BS, (RMAX <= 4 && !STG) ? 3 : 2) k_restrict_w(
   }
 }
 
-// Restriction from a tile: a CTA takes a contiguous range of aggregates
-// (tp.cta_agg), whose rows [r0, r1) are one contiguous range because every
-// aggregate of every level is; the range's rows of u arrive in shared memory
-// by one bulk TMA copy (bounded wait), and one warp per aggregate then forms
-// t = f - A u and fc = P_a^T t as k_restrict_w does.  The aggregates of a
-// coarser level are contiguous ranges of these, so a range covers a compact
-// patch of the grid and most gathers of a sparse stencil fall inside it and
-// are read from shared memory; the others, and f when it is not u, are read
-// from global memory.  The row's P entries and matrix values are requested
-// with its gathers, and each aggregate's CSR slice and P block are
-// requested into L2 as it starts.  Needs K * sizeof(TC) a multiple of 16.
-template <typename TC, int K, int RMAX>
-__global__ void __launch_bounds__(BS, (RMAX <= 4 && sizeof(TC) == 4) ? 3 : 2) k_restrict_t(const int* __restrict__ cta_agg, const int* __restrict__ row_start,
-                                                      const int* __restrict__ coarse_start,
-                                                      const long long* __restrict__ blk_start,
-                                                      const TC* __restrict__ P, const int* __restrict__ rowptr,
-                                                      const int* __restrict__ col, const TC* __restrict__ val,
-                                                      const TC* f, const TC* u, TC* __restrict__ fc,
-                                                      TC* __restrict__ uc, const TC* __restrict__ dinvc,
-                                                      const int* __restrict__ done, Stage sg) {
-  if (*done) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  static_assert((K * sizeof(TC)) % 16 == 0, "tile rows must be whole 16-byte units");
-  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, RPW = 32 / CL;
-  constexpr int RB = 5;  // gathers per batch (most are shared-memory reads)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
-  TC* tile = reinterpret_cast<TC*>(smraw + 16);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane / CL, cl = lane % CL;
-  const int a0 = cta_agg[blockIdx.x], a1 = cta_agg[blockIdx.x + 1];
-  const int r0 = __ldg(row_start + a0), r1 = __ldg(row_start + a1);
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    const unsigned bytes = (unsigned)((size_t)(r1 - r0) * K * sizeof(TC));
-    mbar_expect_tx(bar, bytes);
-    tma_load_1d(tile, u + (size_t)r0 * K, bytes, bar);
-  }
-  __syncthreads();
-  stage_wait(sg, bar, 0);
-  const bool f_in_tile = f == u;
-  auto xload = [&](int c, TC (&xv)[CPT]) {
-    if (c >= r0 && c < r1) {
-      ldp<TC, CPT>(tile + (size_t)(c - r0) * K + cl * CPT, xv);
-    } else {
-      ldv<TC, CPT>(u + (size_t)c * K + cl * CPT, xv);
-    }
-  };
-  for (int a = a0 + warp; a < a1; a += NWARP) {
-    const int rs = __ldg(row_start + a), re = __ldg(row_start + a + 1);
-    const int cs = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - cs;
-    const TC* Pa = P + __ldg(blk_start + a);
-    if (lane == 0) {
-      const int jb = __ldg(rowptr + rs), je = __ldg(rowptr + re);
-      prefetch_l2(col + jb, (size_t)(je - jb) * sizeof(int));
-      prefetch_l2(val + jb, (size_t)(je - jb) * sizeof(TC));
-      prefetch_l2(Pa, (size_t)(re - rs) * ra * sizeof(TC));
-    }
-    TC acc[RMAX][CPT];
-#pragma unroll
-    for (int p = 0; p < RMAX; ++p)
-#pragma unroll
-      for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
-    for (int base = rs; base < re; base += RPW) {
-      const int i = base + g;
-      const bool valid = i < re;
-      TC fv[CPT], pv[RMAX], s[CPT];
-#pragma unroll
-      for (int t = 0; t < CPT; ++t) s[t] = TC(0);
-      if (valid) {
-        if (f_in_tile) ldp<TC, CPT>(tile + (size_t)(i - r0) * K + cl * CPT, fv);
-        else ldv<TC, CPT>(f + (size_t)i * K + cl * CPT, fv);
-        const TC* prow = Pa + (size_t)(i - rs) * ra;
-#pragma unroll
-        for (int p = 0; p < RMAX; ++p) pv[p] = p < ra ? __ldg(prow + p) : TC(0);
-        const int j1 = __ldg(rowptr + i + 1);
-        for (int j = __ldg(rowptr + i); j < j1; j += RB) {
-          int c[RB];
-          TC av[RB], xv[RB][CPT];
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            const bool ok = j + b < j1;
-            c[b] = ok ? __ldg(col + j + b) : -1;
-            av[b] = ok ? __ldg(val + j + b) : TC(0);
-          }
-#pragma unroll
-          for (int b = 0; b < RB; ++b) {
-            if (c[b] >= 0) {
-              xload(c[b], xv[b]);
-            } else {
-#pragma unroll
-              for (int t = 0; t < CPT; ++t) xv[b][t] = TC(0);
-            }
-          }
-#pragma unroll
-          for (int b = 0; b < RB; ++b)
-#pragma unroll
-            for (int t = 0; t < CPT; ++t) s[t] = fma(av[b], xv[b][t], s[t]);
-        }
-#pragma unroll
-        for (int p = 0; p < RMAX; ++p) {
-          if (p < ra) {
-#pragma unroll
-            for (int t = 0; t < CPT; ++t) acc[p][t] = fma(pv[p], fv[t] - s[t], acc[p][t]);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int off = CL; off < 32; off <<= 1)
-#pragma unroll
-      for (int p = 0; p < RMAX; ++p)
-#pragma unroll
-        for (int t = 0; t < CPT; ++t) acc[p][t] += __shfl_xor_sync(FULL, acc[p][t], off);
-    if (g == 0) {
-#pragma unroll
-      for (int p = 0; p < RMAX; ++p) {
-        if (p < ra) {
-          const size_t oc = (size_t)(cs + p) * K + cl * CPT;
-          stv<TC, CPT>(fc + oc, acc[p]);
-          if (uc) {
-            const TC d = __ldg(dinvc + cs + p);
-            TC w[CPT];
-#pragma unroll
-            for (int t = 0; t < CPT; ++t) w[t] = acc[p][t] * d;
-            stv<TC, CPT>(uc + oc, w);
-          }
-        }
-      }
-    }
-  }
-}
-
 // ----------------------------------------------- grouped coarse levels --
 // On a Galerkin level every coarse dof of one aggregate (a row group) has
 // the same column pattern: the coarse dofs of all neighbouring aggregates,

@@ -187,35 +187,6 @@ inline void launch_restrict_g(int K, const Level& L, const Transfer& T, const TP
   AMG_LAUNCH_CHECK();
 }
 
-// The tiled restriction (k_restrict_t) over the CTA ranges of tp; the
-// caller checks restrict_tile_ok first.
-template <typename TC>
-inline bool restrict_tile_ok(int K, const TPart& tp) {
-  return (K * (int)sizeof(TC)) % 16 == 0 && tp.ra_max <= 8 && tp.ncta > 0 &&
-         16 + (size_t)tp.rows_max * K * sizeof(TC) <= 160 * 1024;
-}
-template <typename TC>
-inline void launch_restrict_t(int K, const Level& L, const Transfer& T, const TPart& tp, const Level& C,
-                              bool smooth_next, const TC* f, const TC* u, TC* fc, TC* uc, const int* done,
-                              cudaStream_t st) {
-  if (!restrict_tile_ok<TC>(K, tp)) throw Error(AMG_ERR_INVALID_ARG, "internal: tiled restriction does not fit");
-  const size_t smem = 16 + (size_t)tp.rows_max * K * sizeof(TC);
-  dispatch_k(K, [&](auto kc) {
-    constexpr int KK = decltype(kc)::value;
-    if constexpr ((KK * sizeof(TC)) % 16 == 0) {
-      auto go = [&](auto kern) {
-        ensure_smem(kern, smem);
-        kern<<<tp.ncta, BS, smem, st>>>(tp.cta_agg, T.row_start, T.coarse_start, T.blk_start, pvals<TC>(T),
-                                        L.rowptr, L.col, vals<TC>(L), f, u, fc, smooth_next ? uc : nullptr,
-                                        smooth_next ? dinvs<TC>(C) : nullptr, done, tp.sg);
-      };
-      if (tp.ra_max <= 4) go(k_restrict_t<TC, KK, 4>);
-      else go(k_restrict_t<TC, KK, 8>);
-    }
-  });
-  AMG_LAUNCH_CHECK();
-}
-
 // shared memory of a staged SpMV kernel reading one value array of type TC
 template <typename TC>
 inline size_t csr_stage_bytes(const Stage& sg) {
@@ -256,10 +227,6 @@ inline size_t csr_stage_bytes(const Stage& sg) {
       return;                                                                                          \
     }                                                                                                  \
     if (nzl <= 0) nzl = 1; /* the level is grouped; the CSR kernels take one lane group per row */    \
-    if (tp.tile) {                                                                                     \
-      launch_restrict_t<TC>(K, L, T, tp, C, smooth_next, f, u, fc, uc, done, st);                     \
-      return;                                                                                          \
-    }                                                                                                  \
     if (tp.warp) {                                                                                     \
       dispatch_k(K, [&](auto kc) {                                                                     \
         constexpr int KK = decltype(kc)::value;                                                        \

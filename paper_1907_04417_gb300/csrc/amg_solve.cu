@@ -851,8 +851,7 @@ static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, 
   }
   W.tp[k].warp = warp % 4;         // restriction kernel
   W.tp[k].pwarp = (warp / 4) % 2;  // prolongation kernel
-  W.tp[k].jl = 1 << ((warp / 8) % 4);  // grouped restriction: lanes per group column split
-  W.tp[k].tile = (warp / 32) % 2;  // tiled restriction over the CTA ranges
+  W.tp[k].jl = 1 << (warp / 8);    // grouped restriction: lanes per group column split
   W.t_tp[k] = target;
   W.t_tps[k] = stage;
   W.t_tpw[k] = warp;
@@ -1149,28 +1148,6 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     }
     grp_best = gbest < best || ovr > 0;
   }
-  // the tiled restriction: CTA ranges whose rows of u are staged in shared
-  // memory (one bulk copy), one warp per aggregate
-  bool tile_best = false;
-  if (!grp_best) {
-    Arena tmp3;
-    for (int t : {128, 256, 512, 1024}) {
-      TPart tt = make_tpart(tmp3, P.tr[k], P.lev[k], K, W.err, t);
-      if (!restrict_tile_ok<TC>(K, tt)) continue;
-      if (t > 128 && tt.ncta < sm_count()) break;
-      tt.tile = 1;
-      const float ms = time_tp(tt, 3);
-      if (tune_log()) fprintf(stderr, "[tune] level %d K %d restrict tiled rows %d ncta %d: %.1f us\n", k, K, t,
-                              tt.ncta, ms * 1e3);
-      if (3 * ms < best) {
-        best = 3 * ms;
-        bt = t;
-        bs = 0;
-        tile_best = true;
-      }
-    }
-    AMG_CUDA(cudaDeviceSynchronize());
-  }
   // prolongation: CTA ranges of the chosen partition against one warp per aggregate
   int pw = 0;
   {
@@ -1201,9 +1178,7 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const int jsel = gjl == 4 ? 2 : (gjl == 2 ? 1 : 0);
-  apply_transfer(P, W, k, bt, bs,
-                 (grp_best ? 2 : (tile_best ? 0 : (warp_best ? warp_kind : 0))) + 4 * pw + 8 * jsel +
-                     (tile_best ? 32 : 0));
+  apply_transfer(P, W, k, bt, bs, (grp_best ? 2 : (warp_best ? warp_kind : 0)) + 4 * pw + 8 * jsel);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
