@@ -49,8 +49,8 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
 // one non-zero ahead), and the p.q accumulators live in shared memory, one
 // slot per thread, so that three CTAs fit on an SM.  Offsets into the n x K
 // blocks are 32-bit (n K < 2^32 is checked on the host).
-template <int K, int NZL, bool STG, int OCC = 3>
-__global__ void __launch_bounds__(BS, OCC) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
+template <int K, int NZL, bool STG>
+__global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
                                                    const float* __restrict__ alo, const float* __restrict__ p,
                                                    float* __restrict__ qh, float* __restrict__ ql, KState ks,
@@ -110,8 +110,7 @@ __global__ void __launch_bounds__(BS, OCC) k_cg_q_df(const int* __restrict__ cta
         // predicated batches: every gather of a batch is issued before the
         // first product (a 9-point row in one memory round trip); the
         // double-float steps run on column pairs
-        // OCC CTAs per SM: four take half-depth batches to fit 64 registers
-        constexpr int U = OCC >= 4 ? gather_depth<NZL>() / 2 : gather_depth<NZL>(), NP = CPT / 2;
+        constexpr int U = gather_depth<NZL>(), NP = CPT / 2;
         F2 h2[NP], l2[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) h2[q] = l2[q] = F2{0ull};
@@ -609,7 +608,6 @@ struct Workspace {
   int q_stage = 1;        // whether the double-float q = A p stages its matrix slice
   RPart rq{};             // level-0 row ranges of the double-float q = A p (own CTA size)
   int q_grid = 0;         // > 0: persistent q launch of q_grid CTAs over rq's ranges
-  int q_occ = 3;          // CTAs per SM the double-float q = A p is compiled for (3 or 4)
   // persistent level-0 launches (one system): CTAs of the update, direction
   // and post-smoother kernels, 0 for one CTA per row range
   int upd_grid = 0, p_grid = 0, post_grid = 0;
@@ -1209,7 +1207,7 @@ static void tune_q(Plan& P, Workspace& W) {
   AMG_CUDA(cudaEventCreate(&e0));
   AMG_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bn = W.nzl_q, bs = W.q_stage, bo = 3;
+  int bn = W.nzl_q, bs = W.q_stage;
   long long bt = -1;
   std::vector<int> cand = W.split ? nzl_candidates<float>(W.K) : nzl_candidates<double>(W.K);
   auto time_q = [&](const char* what, long long t, int n, int stage) {
@@ -1245,21 +1243,18 @@ static void tune_q(Plan& P, Workspace& W) {
       if (t > qTargets[0] && rp.ncta < 3 * sm_count()) break;  // under one wave of three CTAs per SM
       W.rq = rp;
       W.ksq = view_state(tmp, W.ks, rp, W.K);
-      for (int occ : {3, 4})
-        for (int stage = rp.sg.enabled; stage >= 0; --stage)
-          for (int n : cand) {
-            W.nzl_q = n;
-            W.q_stage = stage;
-            W.q_occ = occ;
-            float ms = time_q(occ == 4 ? "df occ4" : "df", t, n, stage);
-            if (ms < best) {
-              best = ms;
-              bn = n;
-              bs = stage;
-              bt = t;
-              bo = occ;
-            }
+      for (int stage = rp.sg.enabled; stage >= 0; --stage)
+        for (int n : cand) {
+          W.nzl_q = n;
+          W.q_stage = stage;
+          float ms = time_q("df", t, n, stage);
+          if (ms < best) {
+            best = ms;
+            bn = n;
+            bs = stage;
+            bt = t;
           }
+        }
       AMG_CUDA(cudaDeviceSynchronize());
     }
     // persistent launches (one system): 2 to 4 CTAs per SM walk the chunks,
@@ -1275,24 +1270,19 @@ static void tune_q(Plan& P, Workspace& W) {
           W.rq = rp;
           W.q_grid = grid;
           W.ksq = view_state(tmp, W.ks, flat, W.K);
-          for (int occ : {3, 4}) {
-            if (occ < per_sm) continue;   // the grid must fit at once
-            for (int stage = rp.sg.enabled; stage >= 0; --stage)
-              for (int n : cand) {
-                W.nzl_q = n;
-                W.q_stage = stage;
-                W.q_occ = occ;
-                float ms = time_q(occ == 4 ? "df persistent occ4" : "df persistent", t, n, stage);
-                if (ms < best) {
-                  best = ms;
-                  bn = n;
-                  bs = stage;
-                  bt = t;
-                  bg = grid;
-                  bo = occ;
-                }
+          for (int stage = rp.sg.enabled; stage >= 0; --stage)
+            for (int n : cand) {
+              W.nzl_q = n;
+              W.q_stage = stage;
+              float ms = time_q("df persistent", t, n, stage);
+              if (ms < best) {
+                best = ms;
+                bn = n;
+                bs = stage;
+                bt = t;
+                bg = grid;
               }
-          }
+            }
           AMG_CUDA(cudaDeviceSynchronize());
         }
       }
@@ -1300,7 +1290,6 @@ static void tune_q(Plan& P, Workspace& W) {
     W.rq = keep;
     W.ksq = keep_ks;
     apply_q(P, W, bt, bn, bs, bg);
-    W.q_occ = bo;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1711,7 +1700,6 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     if (t[0] > 0 || t[1] > 0) apply_q(P, *W, t[0], (int)t[1], (int)t[2], (int)t[3]);
     t += 4;
     if (split && P.nsys == 1) apply_persist(*W, (int)t[0], (int)t[1], (int)t[2]);
-    W->q_occ = t[3] == 4 ? 4 : 3;
   }
   std::vector<long long> out;
   if (!cached && autotune) {
@@ -1724,7 +1712,7 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_rp[k], W->t_rps[k], W->t_nzl[k]});
     for (int k = 0; k < nt; ++k) out.insert(out.end(), {W->t_tp[k], W->t_tps[k], W->t_tpw[k]});
     out.insert(out.end(), {W->t_q, W->t_qn, W->t_qs, W->t_qg});
-    out.insert(out.end(), {(long long)W->t_pu, (long long)W->t_pp, (long long)W->t_ppost, (long long)W->q_occ});
+    out.insert(out.end(), {(long long)W->t_pu, (long long)W->t_pp, (long long)W->t_ppost, 0LL});
   }
   if (variant) make_var(P, *W, variant);
   setup_fused_coarse(P, *W, autotune, cached ? (int)tv[6 * nt + 8] : -2);
@@ -1983,9 +1971,7 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
       dispatch_nzl(W.K, W.nzl_q, [&](auto nc) {
         constexpr int NZ = decltype(nc)::value;
         if constexpr (VT<float, KK>::CL * NZ <= 32) {
-          auto kern = W.q_stage && W.rq.sg.enabled
-                          ? (W.q_occ == 4 ? k_cg_q_df<KK, NZ, true, 4> : k_cg_q_df<KK, NZ, true, 3>)
-                          : (W.q_occ == 4 ? k_cg_q_df<KK, NZ, false, 4> : k_cg_q_df<KK, NZ, false, 3>);
+          auto kern = W.q_stage && W.rq.sg.enabled ? k_cg_q_df<KK, NZ, true> : k_cg_q_df<KK, NZ, false>;
           Stage sg = W.rq.sg;
           sg.enabled = sg.enabled && W.q_stage;
           size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
