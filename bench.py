@@ -270,9 +270,10 @@ def algorithmic_bytes(kernel, lv, K, mode="df"):
             return 3 * n * K * 8
         # x, r read and written, p, q read; u0 = D^-1 r stored; (f32c) f0 = fl32(r)
         return 6 * n * K * 8 + n * 8 + n * K * w + (n * K * 4 if mode == "f32c_f64" else 0)
-    if kernel == "cg_direction":  # p = z + b p (df: also x += a p)
-        if mode == "df":                     # z float, p float read/written, x (hi, lo) read/written
-            return n * K * (4 + 8 + 16)
+    if kernel == "cg_direction":  # p = z + b p (df: x stepped after every second iteration)
+        if mode == "df":  # z, p_k read, p_{k+1} written; every second launch also p_{k-1} read and
+            # x (hi, lo) read and written: 12 and 32 bytes per row and column, 22 on average
+            return n * K * 22
         return n * K * (w + 16)              # z, p float64 read and written
     if kernel == "smooth_l0":    # z = u + D^-1 (f - A u) with r.z
         if mode == "df":                     # f = r_hi; r_lo read for r.z

@@ -535,6 +535,7 @@ struct KState {
   const int* sys_grp;  // nsys + 1
   int ngroups;
   double *rho, *alpha, *beta, *bnorm, *rnorm;
+  double* alpha_prev;  // alpha of the previous iteration (the double-float x step runs every second one)
   int *conv, *iters, *status, *active, *done, *iter;
   const int* sys_cta;  // nsys + 1
   int nsys;

@@ -34,6 +34,7 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
           a = 0.0;
         }
       }
+      ks.alpha_prev[v] = ks.alpha[v];
       ks.alpha[v] = a;
     }
     __syncthreads();
@@ -52,10 +53,12 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
 template <int K, int NZL, bool STG>
 __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
-                                                   const float* __restrict__ alo, const float* __restrict__ p,
-                                                   float* __restrict__ qh, float* __restrict__ ql, KState ks,
-                                                   Stage sg, int nchunk) {
+                                                   const float* __restrict__ alo, const float* p0,
+                                                   const float* p1, float* __restrict__ qh,
+                                                   float* __restrict__ ql, KState ks, Stage sg, int nchunk) {
   if (*ks.done) return;
+  // p_k lives in p0 for even k, in p1 for odd k (k the device iteration counter)
+  const float* __restrict__ p = (*ks.iter & 1) ? p1 : p0;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double sm[BS];
   __shared__ double tot[64];
@@ -420,26 +423,36 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
   finish_update<K>(ks, sm, tot);
 }
 
-// x += alpha p (with the alpha of this iteration, x a double-float pair and
-// p an exact float32), then p = fl32(z + beta p); ``first`` starts the
-// recurrence (p = z, x untouched).  Rounding the search direction to float32
-// only perturbs it at the level of the float32 cycle's own rounding: x and r
-// stay consistent because q = A p is formed from the same rounded p.  After
-// the last iteration k_cg_x_df applies the final alpha p, which this kernel
-// skips once every column has stopped.
+// End of iteration k (the device counter already reads k + 1): p_{k+1} =
+// fl32(z + beta p_k), p_k read from its buffer (p0 for even k, p1 for odd k)
+// and p_{k+1} written to the other one; ``first`` starts the recurrence
+// (p_0 = z into p0, x untouched).  The step x += alpha p is taken every
+// second iteration: after an odd k, x += alpha_{k-1} p_{k-1} + alpha_k p_k,
+// with p_{k-1} read from the buffer p_{k+1} then overwrites (x a
+// double-float pair, each p an exact float32), so x is read and written half
+// as often.  Rounding the search direction to float32 only perturbs it at
+// the level of the float32 cycle's own rounding: x and r stay consistent
+// because q = A p is formed from the same rounded p.  After the last
+// iteration k_cg_x_df applies the steps still pending.
 template <int K>
 __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
-                                                float* __restrict__ p, float* __restrict__ xh,
+                                                float* p0, float* p1, float* __restrict__ xh,
                                                 float* __restrict__ xl, KState ks, int first, int nchunk) {
   if (*ks.done) return;
   constexpr int CPT = VT<float, K>::CPT;
   const int cfirst = (int)((threadIdx.x * CPT) % K);
   const int s = cta_system(ks.sys_cta, ks.nsys);
-  float bh[CPT], bl[CPT], ah[CPT], al[CPT];
+  const int k = first ? -1 : *ks.iter - 1;   // the iteration that ends here
+  const bool step = !first && (k & 1);       // an odd k takes the two pending x steps
+  const float* pin = (k & 1) ? p1 : p0;      // p_k
+  float* pout = (k & 1) ? p0 : p1;           // p_{k+1} (after an odd k: where p_{k-1} is)
+  if (first) pout = p0;
+  float bh[CPT], bl[CPT], ah[CPT], al[CPT], ch[CPT], cl[CPT];
 #pragma unroll
   for (int t = 0; t < CPT; ++t) {
     split2(ks.beta[s * K + cfirst + t], bh[t], bl[t]);
     split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+    split2(ks.alpha_prev[s * K + cfirst + t], ch[t], cl[t]);
   }
   for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
   const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
@@ -450,42 +463,62 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
 #pragma unroll
       for (int t = 0; t < CPT; ++t) pv[t] = zv[t];
     } else {
-      float xa[CPT], xb[CPT];
-      ldp<float, CPT>(p + e, pv);
-      ldp<float, CPT>(xh + e, xa);
-      ldp<float, CPT>(xl + e, xb);
+      ldp<float, CPT>(pin + e, pv);
+      if (step) {
+        float po[CPT], xa[CPT], xb[CPT];
+        ldp<float, CPT>(pout + e, po);   // p_{k-1}
+        ldp<float, CPT>(xh + e, xa);
+        ldp<float, CPT>(xl + e, xb);
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) {
-        df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
-        df_norm(xa[t], xb[t]);
-        pv[t] = fmaf(bl[t], pv[t], fmaf(bh[t], pv[t], zv[t]));
+        for (int t = 0; t < CPT; ++t) {
+          df_acc1(ch[t], cl[t], po[t], xa[t], xb[t]);
+          df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
+          df_norm(xa[t], xb[t]);
+        }
+        stv<float, CPT>(xh + e, xa);
+        stv<float, CPT>(xl + e, xb);
       }
-      stv<float, CPT>(xh + e, xa);
-      stv<float, CPT>(xl + e, xb);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) pv[t] = fmaf(bl[t], pv[t], fmaf(bh[t], pv[t], zv[t]));
     }
-    stv<float, CPT>(p + e, pv);
+    stv<float, CPT>(pout + e, pv);
   }
   }
 }
 
-// x += alpha p once after the loop (the step of the last iteration; the
-// alpha of columns that stopped earlier is already zero).
+// The x steps still pending after the last iteration K (kl = K): for an
+// even K, x += alpha_K p_K; for an odd K, x += alpha_{K-1} p_{K-1} +
+// alpha_K p_K (the alphas of columns that stopped earlier are already zero;
+// kl = -1, no iteration, steps by zero).
 template <int K>
-__global__ void __launch_bounds__(BS) k_cg_x_df(const int* __restrict__ cta_row, const float* __restrict__ p,
-                                                float* __restrict__ xh, float* __restrict__ xl, KState ks) {
+__global__ void __launch_bounds__(BS) k_cg_x_df(const int* __restrict__ cta_row, const float* __restrict__ p0,
+                                                const float* __restrict__ p1, float* __restrict__ xh,
+                                                float* __restrict__ xl, KState ks, int kl) {
   constexpr int CPT = VT<float, K>::CPT;
   const int r0 = cta_row[blockIdx.x], r1 = cta_row[blockIdx.x + 1];
   const size_t e0 = (size_t)r0 * K, e1 = (size_t)r1 * K;
   const int cfirst = (int)((threadIdx.x * CPT) % K);
   const int s = cta_system(ks.sys_cta, ks.nsys);
-  float ah[CPT], al[CPT];
+  const bool two = kl >= 1 && (kl & 1);
+  const float* pl = (kl & 1) ? p1 : p0;   // p_K
+  const float* pp = (kl & 1) ? p0 : p1;   // p_{K-1}
+  float ah[CPT], al[CPT], ch[CPT], cl[CPT];
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+  for (int t = 0; t < CPT; ++t) {
+    split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
+    split2(ks.alpha_prev[s * K + cfirst + t], ch[t], cl[t]);
+  }
   for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
     float pv[CPT], xa[CPT], xb[CPT];
-    ldv<float, CPT>(p + e, pv);
+    ldv<float, CPT>(pl + e, pv);
     ldp<float, CPT>(xh + e, xa);
     ldp<float, CPT>(xl + e, xb);
+    if (two) {
+      float po[CPT];
+      ldv<float, CPT>(pp + e, po);
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) df_acc1(ch[t], cl[t], po[t], xa[t], xb[t]);
+    }
 #pragma unroll
     for (int t = 0; t < CPT; ++t) {
       df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
@@ -596,7 +629,8 @@ struct Workspace {
   bool split = false;  // double-float CG vectors (float32-cycle mode)
   bool u0free = false; // split with one pre-sweep: u0 = D^{-1} r_hi is folded into A D^{-1} (never stored)
   float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr;
-  float *ph = nullptr, *qh = nullptr, *ql = nullptr;  // p is float32 (see k_cg_p_df)
+  float *ph = nullptr, *ph2 = nullptr;  // p_k in ph (even k) or ph2 (odd k); float32 (see k_cg_p_df)
+  float *qh = nullptr, *ql = nullptr;
   std::vector<void*> f, u, v;
   KState ks{};
   int* zero_flag = nullptr;
@@ -1610,7 +1644,11 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   W->u0free = split && pre == 1 && P.L > 1;
   if (W->u0free) ensure_scaled(P);
   if (split) {
-    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
+    for (float** v : {&W->xh, &W->xl, &W->rh, &W->rl, &W->ph, &W->ph2, &W->qh, &W->ql}) *v = ar.alloc<float>(n0k);
+    // both direction buffers hold finite values from the start (a pending
+    // step by zero may read either)
+    AMG_CUDA(cudaMemset(W->ph, 0, n0k * sizeof(float)));
+    AMG_CUDA(cudaMemset(W->ph2, 0, n0k * sizeof(float)));
   } else {
     W->p = ar.alloc<double>(n0k);
   }
@@ -1675,6 +1713,9 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
   ks.sg = r0p.sg;
   ks.rho = ar.alloc<double>(nv);
   ks.alpha = ar.alloc<double>(nv);
+  ks.alpha_prev = ar.alloc<double>(nv);
+  AMG_CUDA(cudaMemset(ks.alpha, 0, nv * sizeof(double)));
+  AMG_CUDA(cudaMemset(ks.alpha_prev, 0, nv * sizeof(double)));
   ks.beta = ar.alloc<double>(nv);
   ks.bnorm = ar.alloc<double>(nv);
   ks.rnorm = ar.alloc<double>(nv);
@@ -1977,7 +2018,7 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
           size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
           ensure_smem(kern, smem);
           const int grid = W.q_grid > 0 ? W.q_grid : W.rq.ncta;
-          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.qh, W.ql,
+          kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.ph2, W.qh, W.ql,
                                        W.ksq, sg, W.rq.ncta);
         }
       });
@@ -2025,7 +2066,8 @@ static void launch_cg_p(const Plan& P, Workspace& W, const Level& L, int first, 
     constexpr int KK = decltype(kc)::value;
     if (W.split)
       k_cg_p_df<KK><<<W.p_grid ? W.p_grid : W.rp[0].ncta, BS, 0, st>>>(
-          W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph, W.xh, W.xl, W.ks, first, W.rp[0].ncta);
+          W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.ph, W.ph2, W.xh, W.xl, W.ks, first,
+          W.rp[0].ncta);
     else if (z_is_f32(P, W))
       k_cg_p<KK, float><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, reinterpret_cast<const float*>(W.z), W.p,
                                                      W.ks, first);
@@ -2303,7 +2345,7 @@ amg_status run_pcg(amg_hierarchy* owner, Plan& P, const SolveReq& rq, const amg_
   if (W.split) {
     dispatch_k(K, [&](auto kc) {
       constexpr int KK = decltype(kc)::value;
-      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.ph, W.xh, W.xl, W.ks);
+      k_cg_x_df<KK><<<W.rp[0].ncta, BS, 0, st>>>(W.rp[0].cta_row, W.ph, W.ph2, W.xh, W.xl, W.ks, *W.h_iter - 1);
     });
     AMG_LAUNCH_CHECK();
     launch_pair(false, (long long)W.n0 * K, nullptr, W.xh, W.xl, W.x, nullptr, st);

@@ -58,8 +58,9 @@ def test_roofline_counts_double_float_mode():
     assert ab("spmv_cg") == nnz * 12 + rp + n * K * 4 + n * K * 8
     # q (hi, lo) read, r (hi, lo) read and written
     assert ab("cg_update") == 3 * n * K * 8
-    # z read, p read and written, x (hi, lo) read and written
-    assert ab("cg_direction") == n * K * 28
+    # z and p read, p written; after every second iteration also p_{k-1} and x (hi, lo) read
+    # and x written: 12 and 32 bytes per row and column, 22 per launch on average
+    assert ab("cg_direction") == n * K * 22
     # col + float values, rowptr, D^-1, f = r_hi, u, r_lo read, z written
     assert ab("smooth_l0") == nnz * 8 + rp + n * 4 + 4 * n * K * 4
     # scaled matrix, f read once, P, fc and uc written, D_c^-1 read
