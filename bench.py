@@ -281,6 +281,13 @@ def algorithmic_bytes(kernel, lv, K, mode="df"):
         if mode == "f32c_f64":               # f, u, z float; r float64
             return nnz * 8 + rp + n * 4 + n * K * (4 + 4 + 4 + 8)
         return nnz * 12 + rp + n * 8 + n * K * 8 * 3   # f = r, u, z
+    if kernel == "restrict_l0" and lv.get("rf_entries"):
+        # fc = R f, R = P^T (I - A D^-1) kept by aggregate (pattern offsets and coarse
+        # starts, pattern columns, rf_rs values per entry); f read once, fc and uc
+        # written, D_c^-1 read
+        nagg = lv["nagg1"]
+        return (8 * (nagg + 1) + lv["rf_entries"] * (4 + lv["rf_rs"] * w) + n * K * w
+                + n1 * (2 * K * w + w))
     if kernel == "restrict_l0":  # fc = P^T (f - A u), uc = D_c^-1 fc
         if mode == "df":                     # t = f - (A D^-1) f: one vector block read
             return nnz * 8 + rp + n * K * 4 + npv * 4 + n1 * (2 * K * 4 + 4)
@@ -497,7 +504,12 @@ class Ctx:
             H.timer_enable(0, False)
             ent = {"launches": nl, "ms_total": ms, "avg_ms": ms / max(nl, 1),
                    "share_of_solve": ms / solve_ms if solve_ms > 0 else None}
-            nb = algorithmic_bytes(name, lv, K, mode)
+            lvn = lv
+            if name == "restrict_l0":  # the restriction this solve ran (R or the CSR form)
+                ri = H.restriction_info(0)
+                lvn = dict(lv, rf_entries=ri["entries"] if ri["by_r"] else 0, rf_rs=ri["values_per_entry"])
+                ent["by_r"] = ri["by_r"]
+            nb = algorithmic_bytes(name, lvn, K, mode)
             if nb is not None and nl > 0 and ms > 0:
                 gbs = nb / (ms / nl * 1e-3) / 1e9
                 ent.update({"algorithmic_bytes": nb, "achieved_gbs": gbs, "hbm_frac": gbs / self.peak})
@@ -531,7 +543,7 @@ def level_sizes(H, n0=None, nnz0=None):
     e1 = H.export_level(1)
     i = H.info()
     return {"n0": n0 or i["n_level"][0], "nnz0": nnz0 or i["nnz_level"][0], "n1": e1["n"],
-            "npv1": int(e1["pval"].size)}
+            "npv1": int(e1["pval"].size), "nagg1": int(e1["naggs"])}
 
 
 def true_relres(A, B, X):

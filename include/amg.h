@@ -300,6 +300,21 @@ enum {
 amg_status amg_timer_enable(amg_handle h, int32_t kernel_id, int32_t enable);
 amg_status amg_timer_read(amg_handle h, double* total_ms, int64_t* launches);
 
+/* How the restriction out of level k (0 <= k < levels - 1) ran in the most
+ * recent V-cycle that a solve on this hierarchy (not a batch) enqueued.
+ * With one pre-sweep from zero the iterate that enters the restriction is
+ * u = D^{-1} f, so the restricted residual P^T (f - A u) of Section 5's
+ * V-cycle equals R f with R = P^T (I - A D^{-1}), P the block prolongator
+ * of Eq. (prol).  *by_r (may be NULL) is 1 when the solve applied R (kept
+ * by aggregate: one column pattern per aggregate, the rows its rows of A
+ * reach), 0 when it formed f - A u and applied P^T.  *entries (may be NULL)
+ * receives R's pattern entries (0 while R is not built) and
+ * *values_per_entry (may be NULL) the values stored per entry (the
+ * aggregate's coarse dofs, zero-padded to 4 or 8).  AMG_ERR_INVALID_ARG for
+ * a null handle or k out of range. */
+amg_status amg_restriction_info(amg_handle h, int32_t k, int32_t* by_r, int64_t* entries,
+                                int32_t* values_per_entry);
+
 /*
  * Per-aggregate orthonormal bases, as amg_setup_from_aggregates builds them,
  * computed without any device allocation.  The paper has no counterpart:

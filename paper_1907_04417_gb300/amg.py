@@ -95,6 +95,8 @@ SIGNATURES = {
     "amg_level_colours": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32)]),
     "amg_timer_enable": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "amg_timer_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "amg_restriction_info": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_int32)]),
     "amg_kernel_launches": (C.c_int, [C.POINTER(C.c_int64)]),
     "amg_local_bases_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -332,6 +334,16 @@ class Hierarchy:
         n = C.c_int64()
         _check(lib().amg_timer_read(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def restriction_info(self, k: int) -> dict:
+        """How the most recent V-cycle of a solve restricted out of level k:
+        by_r (R = P^T (I - A D^{-1}) applied), R's pattern entries and values
+        per entry."""
+        by_r = C.c_int32()
+        ent = C.c_int64()
+        rs = C.c_int32()
+        _check(lib().amg_restriction_info(self.h, k, C.byref(by_r), C.byref(ent), C.byref(rs)))
+        return {"by_r": bool(by_r.value), "entries": ent.value, "values_per_entry": rs.value}
 
 
 def _is_torch(a):

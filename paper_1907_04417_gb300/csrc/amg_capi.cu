@@ -276,6 +276,20 @@ amg_status amg_hierarchy_info(amg_handle h, amg_hier_info* info) {
   return AMG_OK;
 }
 
+amg_status amg_restriction_info(amg_handle h, int32_t k, int32_t* by_r, int64_t* entries,
+                                int32_t* values_per_entry) {
+  if (!h) return fail(AMG_ERR_INVALID_ARG, "null handle");
+  return guarded([&]() -> amg_status {
+    const amg::Plan& P = h->plan;
+    AMG_REQUIRE(k >= 0 && k + 1 < P.L, "transfer out of range");
+    const amg::Transfer& T = P.tr[k];
+    if (by_r) *by_r = T.rf_last;
+    if (entries) *entries = T.rf_state == 1 ? T.rf_entries : 0;
+    if (values_per_entry) *values_per_entry = T.rf_state == 1 ? T.rf_rs : 0;
+    return AMG_OK;
+  });
+}
+
 amg_status amg_level_colours(amg_handle h, int32_t k, int32_t* colour, int32_t* ncolours) {
   if (!h) return fail(AMG_ERR_INVALID_ARG, "null handle");
   return guarded([&]() -> amg_status {

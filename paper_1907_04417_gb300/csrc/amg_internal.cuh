@@ -132,6 +132,18 @@ struct Transfer {
   std::vector<long long> h_blk_start;
   int* gagg = nullptr;  // nagg + 1: first row group of the fine level in each aggregate (grouped fine levels)
   Stage gsg;            // staging of the grouped restriction (one CTA per aggregate)
+  // R = P^T (I - A D^{-1}) of the fine level, by aggregate (the restriction
+  // after one pre-sweep from zero): pattern offsets (nagg + 1), pattern
+  // columns, rf_rs values per pattern entry (the aggregate's coarse dofs,
+  // zero-padded); built on first use, rf_state 1 (built) or -1 (not
+  // available: more than 8 coarse dofs in an aggregate, or no float64 level)
+  int rf_state = 0, rf_rs = 4;
+  int rf_last = 0;  // whether the most recently enqueued V-cycle restricted by R
+  long long rf_entries = 0;
+  int* rf_ptr = nullptr;
+  int* rf_col = nullptr;
+  double* rf_v64 = nullptr;
+  float* rf_v32 = nullptr;
 };
 
 // Aggregate-aligned CTA ranges of one transfer for a given column count, with

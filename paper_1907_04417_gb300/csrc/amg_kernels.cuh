@@ -1139,6 +1139,138 @@ __global__ void __launch_bounds__(RG_WARPS * 32) k_restrict_g(
   }
 }
 
+// --------------------------------- restriction by R = P^T (I - A D^{-1}) --
+// With one pre-sweep from zero the iterate that enters the restriction is
+// u = D^{-1} f, so fc = P^T (f - A u) = R f with R = P^T (I - A D^{-1}).
+// All coarse dofs of one aggregate share R's column pattern: the rows that
+// the aggregate's rows of A reach (its halo).  R is stored by aggregate:
+// pattern columns rcol[rptr[a] .. rptr[a+1]) and, per pattern entry, RS
+// values (one per coarse dof of the aggregate, zero-padded to RS).  A warp
+// takes one aggregate at a time (a, then a plus the warps of the grid): CL
+// lanes split the K columns, JL = 32 / CL lane groups split the pattern, U
+// entries per lane group and batch, every gather and value load of a batch
+// requested before its first product.  The next batch's columns (or the next
+// aggregate's first) are requested before the products, the extents two
+// aggregates ahead.  Each halo row of f is gathered once per aggregate,
+// where the CSR restriction gathers it once per non-zero of A.
+
+// Entries per lane group and batch: what keeps the gathered rows, the
+// values and the accumulators of a lane near 100 registers.
+template <typename TC, int K, int RS>
+__host__ __device__ constexpr int rf_batch() {
+  constexpr int w = (int)sizeof(TC) / 4;
+  constexpr int acc = RS * VT<TC, K>::CPT * w, per = (VT<TC, K>::CPT + RS) * w;
+  constexpr int u = (100 - acc) / per;
+  return u < 1 ? 1 : (u > 9 ? 9 : u);
+}
+
+template <typename TC, int K, int RS>
+__global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __restrict__ rptr,
+                                                       const int* __restrict__ rcol, const TC* __restrict__ rval,
+                                                       const int* __restrict__ coarse_start,
+                                                       const TC* __restrict__ f, TC* __restrict__ fc,
+                                                       TC* __restrict__ uc, const TC* __restrict__ dinvc,
+                                                       const int* __restrict__ done) {
+  if (*done) return;
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, JL = 32 / CL, U = rf_batch<TC, K, RS>();
+  constexpr int VP = (16 / (int)sizeof(TC)) < RS ? 16 / (int)sizeof(TC) : RS;  // values per vector load
+  const int lane = threadIdx.x & 31, cl = lane % CL, jl = lane / CL;
+  const int nw = gridDim.x * NWARP;
+  int a = blockIdx.x * NWARP + (threadIdx.x >> 5);
+  auto extent = [&](int g, int& e0, int& e1) {
+    e0 = g < nagg ? __ldg(rptr + g) : 0;
+    e1 = g < nagg ? __ldg(rptr + g + 1) : 0;
+  };
+  // columns of the batch at jb for this lane group (-1 past the pattern)
+  auto cols = [&](int jb, int e1, int(&c)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int jj = jb + jl + u * JL;
+      c[u] = jj < e1 ? __ldg(rcol + jj) : -1;
+    }
+  };
+  int b0, b1, n0, n1;
+  extent(a, b0, b1);
+  extent(a + nw, n0, n1);
+  int c[U];
+  cols(b0, b1, c);
+  for (; a < nagg; a += nw) {
+    int m0, m1;
+    extent(a + 2 * nw, m0, m1);
+    const int c0 = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - c0;
+    TC acc[RS][CPT];
+#pragma unroll
+    for (int p = 0; p < RS; ++p)
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
+    for (int jb = b0;; jb += U * JL) {
+      TC xv[U][CPT], vv[U][RS];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c[u] >= 0) {
+          ldv<TC, CPT>(f + (size_t)c[u] * K + cl * CPT, xv[u]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) xv[u][t] = TC(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const TC* src = rval + (size_t)(jb + jl + u * JL) * RS;
+#pragma unroll
+        for (int q = 0; q < RS; q += VP) {
+          TC piece[VP];
+          if (c[u] >= 0) {
+            ldv<TC, VP>(src + q, piece);
+          } else {
+#pragma unroll
+            for (int e = 0; e < VP; ++e) piece[e] = TC(0);
+          }
+#pragma unroll
+          for (int e = 0; e < VP; ++e) vv[u][q + e] = piece[e];
+        }
+      }
+      // warp-uniform: whether this aggregate has another batch
+      const bool more = jb + U * JL < b1;
+      if (more) cols(jb + U * JL, b1, c);
+      else cols(n0, n1, c);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int p = 0; p < RS; ++p)
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) acc[p][t] = fma(vv[u][p], xv[u][t], acc[p][t]);
+      if (!more) break;
+    }
+    // the lane groups' partial sums, combined by a butterfly (every lane
+    // ends with the same sums)
+#pragma unroll
+    for (int off = CL; off < 32; off <<= 1)
+#pragma unroll
+      for (int p = 0; p < RS; ++p)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) acc[p][t] += __shfl_xor_sync(FULL, acc[p][t], off);
+#pragma unroll
+    for (int p = 0; p < RS; ++p) {
+      if (p < ra && p % JL == jl) {
+        const size_t oc = (size_t)(c0 + p) * K + cl * CPT;
+        stv<TC, CPT>(fc + oc, acc[p]);
+        if (uc) {
+          const TC d = __ldg(dinvc + c0 + p);
+          TC w[CPT];
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) w[t] = acc[p][t] * d;
+          stv<TC, CPT>(uc + oc, w);
+        }
+      }
+    }
+    b0 = n0;
+    b1 = n1;
+    n0 = m0;
+    n1 = m1;
+  }
+}
+
 // u[rows(a)] += P_a uc[coarse(a)]   (aggregate-aligned CTAs)
 template <typename TC, int K>
 __global__ void __launch_bounds__(BS) k_prolong(const int* __restrict__ cta_agg, const int* __restrict__ row_start,

@@ -3,7 +3,10 @@
 // (amg_cycle_f64.cu, amg_cycle_f32.cu) so that they compile in parallel.
 #pragma once
 
+#include <algorithm>
+#include <map>
 #include <type_traits>
+#include <utility>
 
 #include "amg_kernels.cuh"
 
@@ -187,6 +190,37 @@ inline void launch_restrict_g(int K, const Level& L, const Transfer& T, const TP
   AMG_LAUNCH_CHECK();
 }
 
+// Grid of a kernel whose warps walk their work: at most ``need`` CTAs of
+// BS threads, at most as many as stay resident on the device at once (the
+// occupancy of each kernel is looked up once per device).
+template <typename Kern>
+inline int resident_grid(Kern k, long long need) {
+  static std::map<std::pair<const void*, int>, int> cap;
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_pair(reinterpret_cast<const void*>(k), dev);
+  auto it = cap.find(key);
+  if (it == cap.end()) {
+    int per_sm = 0, sms = 0;
+    AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BS, 0));
+    it = cap.emplace(key, std::max(per_sm, 1) * std::max(sms, 1)).first;
+  }
+  return (int)std::max(1LL, std::min(need, (long long)it->second));
+}
+
+template <typename TC>
+inline const TC* rfvals(const Transfer& T) {
+  if constexpr (std::is_same<TC, double>::value) return T.rf_v64; else return T.rf_v32;
+}
+
+// fc = R f (and uc = D_c^{-1} fc) with the aggregate-grouped R of the
+// transfer (built: T.rf_state == 1); a grid of as many CTAs as stay
+// resident, each warp walking aggregates.
+template <typename TC>
+void launch_restrict_rf(int K, const Transfer& T, const Level& C, bool smooth_next, const TC* f, TC* fc, TC* uc,
+                        const int* done, cudaStream_t st);
+
 // shared memory of a staged SpMV kernel reading one value array of type TC
 template <typename TC>
 inline size_t csr_stage_bytes(const Stage& sg) {
@@ -268,6 +302,23 @@ inline size_t csr_stage_bytes(const Stage& sg) {
           throw Error(AMG_ERR_INVALID_ARG, "internal: lane layout too wide");                         \
         }                                                                                              \
       });                                                                                              \
+    });                                                                                                \
+    AMG_LAUNCH_CHECK();                                                                                \
+  }                                                                                                    \
+  template <>                                                                                          \
+  void launch_restrict_rf<TC>(int K, const Transfer& T, const Level& C, bool smooth_next, const TC* f, \
+                              TC* fc, TC* uc, const int* done, cudaStream_t st) {                      \
+    if (T.rf_state != 1) throw Error(AMG_ERR_INVALID_ARG, "internal: restriction operator R not built"); \
+    dispatch_k(K, [&](auto kc) {                                                                       \
+      constexpr int KK = decltype(kc)::value;                                                          \
+      auto go = [&](auto kern) {                                                                       \
+        const int grid = resident_grid(kern, ((long long)T.nagg + NWARP - 1) / NWARP);                 \
+        kern<<<grid, BS, 0, st>>>(T.nagg, T.rf_ptr, T.rf_col, rfvals<TC>(T), T.coarse_start, f, fc,     \
+                                  smooth_next ? uc : nullptr, smooth_next ? dinvs<TC>(C) : nullptr,    \
+                                  done);                                                               \
+      };                                                                                               \
+      if (T.rf_rs == 4) go(k_restrict_rf<TC, KK, 4>);                                                  \
+      else go(k_restrict_rf<TC, KK, 8>);                                                               \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \

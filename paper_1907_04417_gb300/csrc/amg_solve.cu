@@ -656,6 +656,7 @@ struct Workspace {
   int t_pu = 0, t_pp = 0, t_ppost = 0;  // persistent grids of update / p / post
   KState ksq{};           // the CG state seen through the q launch's CTA groups
   std::vector<TPart> tp;  // per transfer: CTA ranges for this column count
+  std::vector<int> rform; // per transfer: restrict by R = P^T (I - A D^{-1}) (one pre-sweep only)
   std::vector<RPart> rp;  // per level: row ranges for this column count
   int* err = nullptr;     // bounded-wait failures of the staged kernels
   cudaGraph_t graph = nullptr;
@@ -878,6 +879,8 @@ static void apply_level(Plan& P, Workspace& W, int k, long long target, int stag
   W.t_rps[k] = stage;
   W.t_nzl[k] = nzl;
 }
+static void ensure_rform(Plan& P, int k);
+static int rform_override();
 static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, int warp) {
   if (target > 0) {
     W.tp[k] = make_tpart(W.ar, P.tr[k], P.lev[k], W.K, W.err, target);
@@ -885,7 +888,17 @@ static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, 
   }
   W.tp[k].warp = warp % 4;         // restriction kernel
   W.tp[k].pwarp = (warp / 4) % 2;  // prolongation kernel
-  W.tp[k].jl = 1 << (warp / 8);    // grouped restriction: lanes per group column split
+  W.tp[k].jl = 1 << ((warp / 8) % 4);  // grouped restriction: lanes per group column split
+  // restriction by R (one pre-sweep): replaces the restriction kernel above
+  // in the V-cycle; the variant cycles keep the CSR restriction
+  int rf = (warp / 32) % 2;
+  const int rov = rform_override();
+  if (rov != 0) rf = rov > 0 ? 1 : 0;
+  if (rf && W.pre == 1) ensure_rform(P, k);
+  if (P.tr[k].rf_state != 1 || W.pre != 1) rf = 0;
+  if ((int)W.rform.size() < P.L - 1) W.rform.assign(std::max(P.L - 1, 0), 0);
+  W.rform[k] = rf;
+  warp = warp % 32 + 32 * rf;
   W.t_tp[k] = target;
   W.t_tps[k] = stage;
   W.t_tpw[k] = warp;
@@ -1209,10 +1222,50 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
     }
     AMG_CUDA(cudaDeviceSynchronize());
   }
+  const int jsel = gjl == 4 ? 2 : (gjl == 2 ? 1 : 0);
+  const int code = (grp_best ? 2 : (warp_best ? warp_kind : 0)) + 4 * pw + 8 * jsel;
+  // restriction by R = P^T (I - A D^{-1}) (one pre-sweep): alternating
+  // re-timings against the restriction chosen above
+  int rf = 0;
+  if (W.pre == 1 && rform_override() == 0) {
+    ensure_rform(P, k);
+    if (P.tr[k].rf_state == 1) {
+      Arena tmp3;
+      TPart tc = bt > 0 ? make_tpart(tmp3, P.tr[k], P.lev[k], K, W.err, bt) : W.tp[k];
+      if (bt > 0) tc.sg.enabled = tc.sg.enabled && bs;
+      tc.warp = code % 4;
+      tc.pwarp = (code / 4) % 2;
+      tc.jl = 1 << ((code / 8) % 4);
+      const bool nxt = k + 1 < P.L - 1;
+      auto run_rf = [&] {
+        launch_restrict_rf<TC>(K, P.tr[k], P.lev[k + 1], nxt, static_cast<TC*>(W.f[k]),
+                               static_cast<TC*>(W.f[k + 1]), static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
+      };
+      auto time_rf = [&](int reps) {
+        run_rf();
+        AMG_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < reps; ++r) run_rf();
+        AMG_CUDA(cudaEventRecord(e1, 0));
+        AMG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return ms / reps;
+      };
+      float mc = 1e30f, mr = 1e30f;
+      for (int round = 0; round < 3; ++round) {
+        mc = std::min(mc, time_tp(tc, 5));
+        mr = std::min(mr, time_rf(5));
+      }
+      if (tune_log())
+        fprintf(stderr, "[tune] level %d K %d restrict by R: %.1f us against %.1f us\n", k, K, mr * 1e3,
+                mc * 1e3);
+      rf = mr < mc ? 1 : 0;
+      AMG_CUDA(cudaDeviceSynchronize());
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  const int jsel = gjl == 4 ? 2 : (gjl == 2 ? 1 : 0);
-  apply_transfer(P, W, k, bt, bs, (grp_best ? 2 : (warp_best ? warp_kind : 0)) + 4 * pw + 8 * jsel);
+  apply_transfer(P, W, k, bt, bs, code + 32 * rf);
 }
 
 static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st);
@@ -1534,6 +1587,98 @@ static void ensure_scaled(Plan& P) {
   AMG_CUDA(cudaDeviceSynchronize());
 }
 
+// R = P^T (I - A D^{-1}) of transfer k (the restriction after one pre-sweep
+// from zero), built once per plan on the host from the float64 level and
+// prolongator: for aggregate a with rows I_a and coarse dofs c,
+//   R[c, h] = P[h, c] [h in I_a] - sum_{i in I_a} P[i, c] a_ih / d_h,
+// h over the sorted halo of a (I_a and every column of its rows), the P term
+// first and then the rows of A in order.  float64 and float32 copies, RS = 4
+// or 8 values per pattern entry; 16 zero entries of padding.
+static void ensure_rform(Plan& P, int k) {
+  Transfer& T = P.tr[k];
+  if (T.rf_state != 0) return;
+  T.rf_state = -1;
+  AMG_CUDA(cudaDeviceSynchronize());  // the plan's arrays may still be in flight on the setup stream
+  const Level& L = P.lev[k];
+  if (k + 1 >= P.L || !L.dinv64 || !L.val64 || !T.p64 || T.nagg <= 0) return;
+  if ((int)L.h_rowptr.size() != L.n + 1 || (int)T.h_row_start.size() != T.nagg + 1 ||
+      (int)T.h_coarse_start.size() != T.nagg + 1 || (int)T.h_blk_start.size() != T.nagg + 1)
+    return;
+  const std::vector<int>& rs = T.h_row_start;
+  const std::vector<int>& cs = T.h_coarse_start;
+  int ramax = 0;
+  for (int a = 0; a < T.nagg; ++a) ramax = std::max(ramax, cs[a + 1] - cs[a]);
+  if (ramax < 1 || ramax > 8) return;
+  const int RS = ramax <= 4 ? 4 : 8;
+  std::vector<int> col(L.nnz);
+  std::vector<double> val(L.nnz), dinv(L.n), pv(T.npval);
+  AMG_CUDA(cudaMemcpy(col.data(), L.col, col.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  AMG_CUDA(cudaMemcpy(val.data(), L.val64, val.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  AMG_CUDA(cudaMemcpy(dinv.data(), L.dinv64, dinv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  AMG_CUDA(cudaMemcpy(pv.data(), T.p64, pv.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  std::vector<int> ptr(T.nagg + 1, 0), pcol, halo;
+  std::vector<double> pval;
+  pcol.reserve((size_t)L.nnz / 2 + 16);
+  pval.reserve(pcol.capacity() * RS);
+  for (int a = 0; a < T.nagg; ++a) {
+    const int r0 = rs[a], r1 = rs[a + 1], ra = cs[a + 1] - cs[a];
+    if (r0 < 0 || r1 > L.n || r1 < r0) return;
+    const double* Pa = pv.data() + T.h_blk_start[a];
+    halo.clear();
+    for (int i = r0; i < r1; ++i) {
+      halo.push_back(i);
+      for (int j = L.h_rowptr[i]; j < L.h_rowptr[i + 1]; ++j) {
+        if (col[j] < 0 || col[j] >= L.n) return;
+        halo.push_back(col[j]);
+      }
+    }
+    std::sort(halo.begin(), halo.end());
+    halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+    const size_t base = pcol.size();
+    if (base + halo.size() >= (size_t)INT32_MAX - 64) return;
+    pcol.insert(pcol.end(), halo.begin(), halo.end());
+    pval.resize(pcol.size() * RS, 0.0);
+    double* V = pval.data() + base * RS;
+    auto pos = [&](int h) { return (size_t)(std::lower_bound(halo.begin(), halo.end(), h) - halo.begin()); };
+    for (int i = r0; i < r1; ++i) {
+      const size_t hi = pos(i);
+      for (int p = 0; p < ra; ++p) V[hi * RS + p] += Pa[(size_t)(i - r0) * ra + p];
+    }
+    for (int i = r0; i < r1; ++i)
+      for (int j = L.h_rowptr[i]; j < L.h_rowptr[i + 1]; ++j) {
+        const size_t h = pos(col[j]);
+        const double w = val[j] * dinv[col[j]];
+        for (int p = 0; p < ra; ++p) V[h * RS + p] -= Pa[(size_t)(i - r0) * ra + p] * w;
+      }
+    ptr[a + 1] = (int)pcol.size();
+  }
+  const size_t ne = pcol.size();
+  pcol.resize(ne + 16, 0);
+  pval.resize((ne + 16) * RS, 0.0);
+  std::vector<float> pv32(pval.size());
+  for (size_t e = 0; e < pval.size(); ++e) pv32[e] = (float)pval[e];
+  T.rf_ptr = P.arena->alloc<int>(ptr.size());
+  T.rf_col = P.arena->alloc<int>(pcol.size());
+  T.rf_v64 = P.arena->alloc<double>(pval.size());
+  T.rf_v32 = P.arena->alloc<float>(pv32.size());
+  AMG_CUDA(cudaMemcpy(T.rf_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  AMG_CUDA(cudaMemcpy(T.rf_col, pcol.data(), pcol.size() * sizeof(int), cudaMemcpyHostToDevice));
+  AMG_CUDA(cudaMemcpy(T.rf_v64, pval.data(), pval.size() * sizeof(double), cudaMemcpyHostToDevice));
+  AMG_CUDA(cudaMemcpy(T.rf_v32, pv32.data(), pv32.size() * sizeof(float), cudaMemcpyHostToDevice));
+  T.rf_rs = RS;
+  T.rf_entries = (long long)ne;
+  T.rf_state = 1;
+}
+
+// AMG_RESTRICT_RFORM in the environment overrides the tuner's choice of the
+// restriction by R = P^T (I - A D^{-1}) (one pre-sweep only): "1" takes it on
+// every transfer that has it, "0" never; unset, timing decides.
+static int rform_override() {
+  const char* e = std::getenv("AMG_RESTRICT_RFORM");
+  if (!e || !*e) return 0;
+  return e[0] == '1' ? 1 : (e[0] == '0' ? -1 : 0);
+}
+
 static void make_var(Plan& P, Workspace& W, int variant);
 
 // Test hook: AMG_TEST_FIRST_WAIT=n (1..15) limits the first wait for every
@@ -1755,6 +1900,8 @@ static Workspace& get_ws(Plan& P, int K, int prec, int pre, int post, bool split
     out.insert(out.end(), {W->t_q, W->t_qn, W->t_qs, W->t_qg});
     out.insert(out.end(), {(long long)W->t_pu, (long long)W->t_pp, (long long)W->t_ppost, 0LL});
   }
+  if (!cached && !autotune && rform_override() > 0)  // untuned workspaces take R only when forced
+    for (int k = 0; k < nt; ++k) apply_transfer(P, *W, k, 0, 0, W->tp[k].warp + 4 * W->tp[k].pwarp);
   if (variant) make_var(P, *W, variant);
   setup_fused_coarse(P, *W, autotune, cached ? (int)tv[6 * nt + 8] : -2);
   if (autotune && !cached) {
@@ -1896,6 +2043,7 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
   std::unique_ptr<TimedLaunch> coarse_span;
   // with the fused small-level cycle the restrictions stop at its start level
   const int kdown = W.cc_s > 0 ? W.cc_s : L - 1;
+  for (int k = 0; k + 1 < L; ++k) P.tr[k].rf_last = 0;
   for (int k = 0; k < kdown; ++k) {
     if (k == 1) coarse_span.reset(new TimedLaunch(h, AMG_KERNEL_COARSE_LEVELS, st, pool));
     for (int s = 1; s < W.pre; ++s) {
@@ -1905,7 +2053,12 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
     bool smooth_next = (k + 1 < L - 1);
     {
       TimedLaunch tl(h, k == 0 ? AMG_KERNEL_RESTRICT_L0 : -1, st, pool);
-      if (k == 0 && W.u0free) {
+      const bool by_r = W.pre == 1 && k < (int)W.rform.size() && W.rform[k];
+      P.tr[k].rf_last = by_r ? 1 : 0;
+      if (by_r) {
+        // fc = R f: the iterate entering the restriction is D^{-1} f
+        launch_restrict_rf<TC>(K, P.tr[k], P.lev[k + 1], smooth_next, F(k), F(k + 1), cur[k + 1], done, st);
+      } else if (k == 0 && W.u0free) {
         // t = f - A D^{-1} f: the first pre-sweep from zero is folded into the
         // column-scaled matrix, so u0 = D^{-1} f is never stored
         Level L0s = P.lev[0];

@@ -98,3 +98,22 @@ def test_double_float_counts_at_the_headline_size():
 def test_whole_job_value_is_per_rhs_over_all_ranks():
     assert bench.whole_job_ms_per_rhs(1000.0, 5, 32, 1) == pytest.approx(1000.0 / 5 / 32)
     assert bench.whole_job_ms_per_rhs(1000.0, 5, 32, 4) == pytest.approx(1000.0 / 5 / 128)
+
+
+def test_restriction_by_r_counts():
+    """With R = P^T (I - A D^-1) (one pre-sweep) the level-0 restriction reads
+    R once (pattern offsets and coarse starts, 4-byte columns, values per
+    entry), f once, D_c^-1 once, and writes fc and uc."""
+    nagg, ent, rs = 250, 250 * 36, 4
+    lv = dict(LV, nagg1=nagg, rf_entries=ent, rf_rs=rs)
+    for mode, w in (("df", 4), ("f32c_f64", 4), ("f64", 8)):
+        assert bench.algorithmic_bytes("restrict_l0", lv, K, mode) == (
+            8 * (nagg + 1) + ent * (4 + rs * w) + n * K * w + n1 * (2 * K * w + w))
+    # without R the CSR count stands
+    assert bench.algorithmic_bytes("restrict_l0", dict(lv, rf_entries=0), K, "df") == \
+        bench.algorithmic_bytes("restrict_l0", LV, K, "df")
+    # at 1024^2, 32 columns, aggregates of 16 with 4 x 4 blocks of a 9-point stencil
+    # (36 halo rows each): 248 MB, against 299 MB for the CSR form
+    big = {"n0": 1048576, "nnz0": 9424900, "n1": 262144, "npv1": 4194304, "nagg1": 65536,
+           "rf_entries": 65536 * 36, "rf_rs": 4}
+    assert bench.algorithmic_bytes("restrict_l0", big, 32, "df") == pytest.approx(248e6, rel=0.01)
