@@ -117,6 +117,16 @@ struct Level {
   int grp_ok = 0, ngrp = 0, grp_rmax = 0;
   const int* gstart = nullptr;
   Stage gsg;  // staging of the grouped sweep's CTAs (GROUPS_PER_CTA groups each)
+  // entry-major copy of a grouped level for the warp-per-group sweep: per
+  // row group its pattern (gw_col from gw_ptr[g]) and, per pattern entry,
+  // gw_rs values (the group's rows, zero-padded to 4 or 8); built on first
+  // use, gw_state 1 (built) or -1 (not available)
+  int gw_state = 0, gw_rs = 4;
+  int gw_zero = 0;  // first entry of the zero batch (patterns padded to multiples of 8)
+  int* gw_ptr = nullptr;
+  int* gw_col = nullptr;
+  double* gw_v64 = nullptr;
+  float* gw_v32 = nullptr;
 };
 
 // P^{k+1}: maps level k+1 (coarse) to level k (fine).
@@ -139,7 +149,8 @@ struct Transfer {
   // available: more than 8 coarse dofs in an aggregate, or no float64 level)
   int rf_state = 0, rf_rs = 4;
   int rf_last = 0;  // whether the most recently enqueued V-cycle restricted by R
-  long long rf_entries = 0;
+  long long rf_entries = 0;  // pattern entries, each aggregate's padded to a multiple of 8
+  int rf_zero = 0;           // first entry of the zero batch after the last aggregate
   int* rf_ptr = nullptr;
   int* rf_col = nullptr;
   double* rf_v64 = nullptr;

@@ -1164,13 +1164,22 @@ __host__ __device__ constexpr int rf_batch() {
   return u < 1 ? 1 : (u > 9 ? 9 : u);
 }
 
-template <typename TC, int K, int RS>
-__global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __restrict__ rptr,
-                                                       const int* __restrict__ rcol, const TC* __restrict__ rval,
-                                                       const int* __restrict__ coarse_start,
-                                                       const TC* __restrict__ f, TC* __restrict__ fc,
-                                                       TC* __restrict__ uc, const TC* __restrict__ dinvc,
-                                                       const int* __restrict__ done) {
+// The same walk serves the l1-Jacobi sweep of a grouped level (EPI 1):
+// there the groups are the level's row groups (the coarse dofs of one
+// aggregate of the level above, one shared pattern) with an entry-major copy
+// of the level's values, the gathered vector is the iterate u, and the
+// epilogue writes v = u + D^{-1} (f - A u) on the group's rows.
+// EPI 0: ostart = coarse_start, x = f, out = fc, out2 = uc (may be null),
+//        d = D_c^{-1}.
+// EPI 1: ostart = the row groups' starts, x = u, out = v, d = D^{-1},
+//        fo = f (u's own rows are read from x).
+template <typename TC, int K, int RS, int EPI>
+__global__ void __launch_bounds__(BS, 2) k_group_rf(int ngrp, const int* __restrict__ rptr,
+                                                    const int* __restrict__ rcol, const TC* __restrict__ rval,
+                                                    const int* __restrict__ ostart, const TC* __restrict__ x,
+                                                    TC* __restrict__ out, TC* __restrict__ out2,
+                                                    const TC* __restrict__ d, const TC* __restrict__ fo,
+                                                    const int* __restrict__ done) {
   if (*done) return;
   constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, JL = 32 / CL, U = rf_batch<TC, K, RS>();
   constexpr int VP = (16 / (int)sizeof(TC)) < RS ? 16 / (int)sizeof(TC) : RS;  // values per vector load
@@ -1178,8 +1187,8 @@ __global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __re
   const int nw = gridDim.x * NWARP;
   int a = blockIdx.x * NWARP + (threadIdx.x >> 5);
   auto extent = [&](int g, int& e0, int& e1) {
-    e0 = g < nagg ? __ldg(rptr + g) : 0;
-    e1 = g < nagg ? __ldg(rptr + g + 1) : 0;
+    e0 = g < ngrp ? __ldg(rptr + g) : 0;
+    e1 = g < ngrp ? __ldg(rptr + g + 1) : 0;
   };
   // columns of the batch at jb for this lane group (-1 past the pattern)
   auto cols = [&](int jb, int e1, int(&c)[U]) {
@@ -1194,10 +1203,10 @@ __global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __re
   extent(a + nw, n0, n1);
   int c[U];
   cols(b0, b1, c);
-  for (; a < nagg; a += nw) {
+  for (; a < ngrp; a += nw) {
     int m0, m1;
     extent(a + 2 * nw, m0, m1);
-    const int c0 = __ldg(coarse_start + a), ra = __ldg(coarse_start + a + 1) - c0;
+    const int c0 = __ldg(ostart + a), ra = __ldg(ostart + a + 1) - c0;
     TC acc[RS][CPT];
 #pragma unroll
     for (int p = 0; p < RS; ++p)
@@ -1208,7 +1217,7 @@ __global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __re
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (c[u] >= 0) {
-          ldv<TC, CPT>(f + (size_t)c[u] * K + cl * CPT, xv[u]);
+          ldv<TC, CPT>(x + (size_t)c[u] * K + cl * CPT, xv[u]);
         } else {
 #pragma unroll
           for (int t = 0; t < CPT; ++t) xv[u][t] = TC(0);
@@ -1230,7 +1239,7 @@ __global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __re
           for (int e = 0; e < VP; ++e) vv[u][q + e] = piece[e];
         }
       }
-      // warp-uniform: whether this aggregate has another batch
+      // warp-uniform: whether this group has another batch
       const bool more = jb + U * JL < b1;
       if (more) cols(jb + U * JL, b1, c);
       else cols(n0, n1, c);
@@ -1254,13 +1263,23 @@ __global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __re
     for (int p = 0; p < RS; ++p) {
       if (p < ra && p % JL == jl) {
         const size_t oc = (size_t)(c0 + p) * K + cl * CPT;
-        stv<TC, CPT>(fc + oc, acc[p]);
-        if (uc) {
-          const TC d = __ldg(dinvc + c0 + p);
-          TC w[CPT];
+        if constexpr (EPI == 0) {
+          stv<TC, CPT>(out + oc, acc[p]);
+          if (out2) {
+            const TC dp = __ldg(d + c0 + p);
+            TC w[CPT];
 #pragma unroll
-          for (int t = 0; t < CPT; ++t) w[t] = acc[p][t] * d;
-          stv<TC, CPT>(uc + oc, w);
+            for (int t = 0; t < CPT; ++t) w[t] = acc[p][t] * dp;
+            stv<TC, CPT>(out2 + oc, w);
+          }
+        } else {
+          const TC dp = __ldg(d + c0 + p);
+          TC fv[CPT], uv[CPT], w[CPT];
+          ldv<TC, CPT>(fo + oc, fv);
+          ldv<TC, CPT>(x + oc, uv);
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) w[t] = fma(dp, fv[t] - acc[p][t], uv[t]);
+          stv<TC, CPT>(out + oc, w);
         }
       }
     }
@@ -1268,6 +1287,135 @@ __global__ void __launch_bounds__(BS, 2) k_restrict_rf(int nagg, const int* __re
     b1 = n1;
     n0 = m0;
     n1 = m1;
+  }
+}
+
+// The slot form of the same product.  Patterns are padded to a multiple of
+// RF_PAD entries (a valid column with zero values) and a batch of RF_PAD zero
+// entries follows the last group (at zero_e), so that every batch is full
+// and a slot past the end of its pattern reads the zero batch instead of
+// taking a branch.  A slot of CL lanes walks one group alone, U entries per
+// batch (U divides RF_PAD), 32 / CL slots per warp on consecutive groups; the
+// warp runs as many batches as its longest group, and no lane-group sums are
+// combined.  The columns of the next batch (or of the next pass's first) are
+// requested with the current batch, the extents two passes ahead.
+constexpr int RF_PAD = 8;
+template <typename TC, int K, int RS>
+__host__ __device__ constexpr int rs_batch() {
+  constexpr int w = (int)sizeof(TC) / 4;
+  constexpr int acc = RS * VT<TC, K>::CPT * w, per = (VT<TC, K>::CPT + RS) * w;
+  return acc + 8 * per <= 100 ? 8 : (acc + 4 * per <= 100 ? 4 : (acc + 2 * per <= 100 ? 2 : 1));
+}
+template <int U>
+__device__ __forceinline__ void ld_cols(const int* __restrict__ p, int (&c)[U]) {
+  if constexpr (U == 8) {
+    const int4 a = __ldg(reinterpret_cast<const int4*>(p)), b = __ldg(reinterpret_cast<const int4*>(p) + 1);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+  } else if constexpr (U == 4) {
+    const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+  } else if constexpr (U == 2) {
+    const int2 a = __ldg(reinterpret_cast<const int2*>(p));
+    c[0] = a.x; c[1] = a.y;
+  } else {
+    c[0] = __ldg(p);
+  }
+}
+template <typename TC, int K, int RS, int EPI>
+__global__ void __launch_bounds__(BS, 2) k_group_rs(int ngrp, int zero_e, const int* __restrict__ rptr,
+                                                    const int* __restrict__ rcol, const TC* __restrict__ rval,
+                                                    const int* __restrict__ ostart, const TC* __restrict__ x,
+                                                    TC* __restrict__ out, TC* __restrict__ out2,
+                                                    const TC* __restrict__ d, const TC* __restrict__ fo,
+                                                    const int* __restrict__ done) {
+  if (*done) return;
+  constexpr int CPT = VT<TC, K>::CPT, CL = VT<TC, K>::CL, SPW = 32 / CL, U = rs_batch<TC, K, RS>();
+  constexpr int VP = (16 / (int)sizeof(TC)) < RS ? 16 / (int)sizeof(TC) : RS;  // values per vector load
+  static_assert(RF_PAD % U == 0, "a batch must divide the pattern padding");
+  const int lane = threadIdx.x & 31, cl = lane % CL, slot = lane / CL;
+  const int nw = gridDim.x * NWARP, npass = (ngrp + SPW - 1) / SPW;
+  int pass = blockIdx.x * NWARP + (threadIdx.x >> 5);
+  // this slot's group in pass q: first entry and number of batches
+  auto extent = [&](int q, int& e0, int& nb) {
+    const int g = q * SPW + slot;
+    if (g < ngrp) {
+      e0 = __ldg(rptr + g);
+      nb = (__ldg(rptr + g + 1) - e0) / U;
+    } else {
+      e0 = zero_e;
+      nb = 0;
+    }
+  };
+  int e0, nb, f0, fnb;
+  extent(pass, e0, nb);
+  extent(pass + nw, f0, fnb);
+  int c[U];
+  ld_cols<U>(rcol + (nb > 0 ? e0 : zero_e), c);
+  for (; pass < npass; pass += nw) {
+    int h0, hnb;
+    extent(pass + 2 * nw, h0, hnb);
+    const int g = pass * SPW + slot;
+    const int c0 = g < ngrp ? __ldg(ostart + g) : 0, ra = g < ngrp ? __ldg(ostart + g + 1) - c0 : 0;
+    const int nbw = (int)__reduce_max_sync(FULL, (unsigned)nb);
+    TC acc[RS][CPT];
+#pragma unroll
+    for (int p = 0; p < RS; ++p)
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) acc[p][t] = TC(0);
+    for (int b = 0; b < nbw; ++b) {
+      const int eb = b < nb ? e0 + b * U : zero_e;
+      TC xv[U][CPT], vv[U][RS];
+#pragma unroll
+      for (int u = 0; u < U; ++u) ldv<TC, CPT>(x + (size_t)c[u] * K + cl * CPT, xv[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int q = 0; q < RS; q += VP) {
+          TC piece[VP];
+          ldv<TC, VP>(rval + (size_t)(eb + u) * RS + q, piece);
+#pragma unroll
+          for (int e = 0; e < VP; ++e) vv[u][q + e] = piece[e];
+        }
+      }
+      const int en = b + 1 < nbw ? (b + 1 < nb ? e0 + (b + 1) * U : zero_e) : (fnb > 0 ? f0 : zero_e);
+      ld_cols<U>(rcol + en, c);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int p = 0; p < RS; ++p)
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) acc[p][t] = fma(vv[u][p], xv[u][t], acc[p][t]);
+    }
+    if (nbw == 0) ld_cols<U>(rcol + (fnb > 0 ? f0 : zero_e), c);
+#pragma unroll
+    for (int p = 0; p < RS; ++p) {
+      if (p < ra) {
+        const size_t oc = (size_t)(c0 + p) * K + cl * CPT;
+        if constexpr (EPI == 0) {
+          stv<TC, CPT>(out + oc, acc[p]);
+          if (out2) {
+            const TC dp = __ldg(d + c0 + p);
+            TC w[CPT];
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) w[t] = acc[p][t] * dp;
+            stv<TC, CPT>(out2 + oc, w);
+          }
+        } else {
+          const TC dp = __ldg(d + c0 + p);
+          TC fv[CPT], uv[CPT], w[CPT];
+          ldv<TC, CPT>(fo + oc, fv);
+          ldv<TC, CPT>(x + oc, uv);
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) w[t] = fma(dp, fv[t] - acc[p][t], uv[t]);
+          stv<TC, CPT>(out + oc, w);
+        }
+      }
+    }
+    e0 = f0;
+    nb = fnb;
+    f0 = h0;
+    fnb = hnb;
   }
 }
 

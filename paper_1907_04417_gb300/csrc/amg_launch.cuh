@@ -217,9 +217,21 @@ inline const TC* rfvals(const Transfer& T) {
 // fc = R f (and uc = D_c^{-1} fc) with the aggregate-grouped R of the
 // transfer (built: T.rf_state == 1); a grid of as many CTAs as stay
 // resident, each warp walking aggregates.
+// kind 1: a warp per aggregate, its lane groups splitting the pattern
+// (k_group_rf); kind 2: a slot of lanes per aggregate (k_group_rs)
 template <typename TC>
 void launch_restrict_rf(int K, const Transfer& T, const Level& C, bool smooth_next, const TC* f, TC* fc, TC* uc,
-                        const int* done, cudaStream_t st);
+                        const int* done, cudaStream_t st, int kind);
+
+template <typename TC>
+inline const TC* gwvals(const Level& L) {
+  if constexpr (std::is_same<TC, double>::value) return L.gw_v64; else return L.gw_v32;
+}
+// Lane code of the warp-per-group sweep of a grouped level (launch_smooth's
+// nzl; codes <= 0 above it are the CTA-per-groups sweep, -jl lanes per split)
+constexpr int NZL_GROUP_WARP = -16;
+// ... and of the slot form (a slot of lanes per row group, k_group_rs)
+constexpr int NZL_GROUP_SLOT = -17;
 
 // shared memory of a staged SpMV kernel reading one value array of type TC
 template <typename TC>
@@ -231,6 +243,33 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   template <>                                                                                          \
   void launch_smooth<TC>(int K, int nzl, const Level& L, const RPart& rp, const TC* f, const TC* u,   \
                          TC* v, const int* done, cudaStream_t st) {                                    \
+    if (nzl == NZL_GROUP_WARP || nzl == NZL_GROUP_SLOT) { /* grouped level, entry-major copy */     \
+      if (L.gw_state != 1) throw Error(AMG_ERR_INVALID_ARG, "internal: grouped copy not built");      \
+      dispatch_k(K, [&](auto kc) {                                                                     \
+        constexpr int KK = decltype(kc)::value;                                                        \
+        if (nzl == NZL_GROUP_WARP) {                                                                   \
+          auto go = [&](auto kern) {                                                                   \
+            const int grid = resident_grid(kern, ((long long)L.ngrp + NWARP - 1) / NWARP);             \
+            kern<<<grid, BS, 0, st>>>(L.ngrp, L.gw_ptr, L.gw_col, gwvals<TC>(L), L.gstart, u, v,        \
+                                      nullptr, dinvs<TC>(L), f, done);                                 \
+          };                                                                                           \
+          if (L.gw_rs == 4) go(k_group_rf<TC, KK, 4, 1>);                                              \
+          else go(k_group_rf<TC, KK, 8, 1>);                                                           \
+        } else {                                                                                       \
+          constexpr int SPW = 32 / VT<TC, KK>::CL;                                                     \
+          auto go = [&](auto kern) {                                                                   \
+            const long long passes = ((long long)L.ngrp + SPW - 1) / SPW;                              \
+            const int grid = resident_grid(kern, (passes + NWARP - 1) / NWARP);                        \
+            kern<<<grid, BS, 0, st>>>(L.ngrp, L.gw_zero, L.gw_ptr, L.gw_col, gwvals<TC>(L), L.gstart,  \
+                                      u, v, nullptr, dinvs<TC>(L), f, done);                           \
+          };                                                                                           \
+          if (L.gw_rs == 4) go(k_group_rs<TC, KK, 4, 1>);                                              \
+          else go(k_group_rs<TC, KK, 8, 1>);                                                           \
+        }                                                                                              \
+      });                                                                                              \
+      AMG_LAUNCH_CHECK();                                                                              \
+      return;                                                                                          \
+    }                                                                                                  \
     if (nzl <= 0) { /* grouped coarse level, -nzl lanes per group column split (0: one) */            \
       launch_smooth_g<TC>(K, nzl < 0 ? -nzl : 1, L, f, u, v, done, st, rp.sg.err);                    \
       return;                                                                                          \
@@ -307,18 +346,31 @@ inline size_t csr_stage_bytes(const Stage& sg) {
   }                                                                                                    \
   template <>                                                                                          \
   void launch_restrict_rf<TC>(int K, const Transfer& T, const Level& C, bool smooth_next, const TC* f, \
-                              TC* fc, TC* uc, const int* done, cudaStream_t st) {                      \
+                              TC* fc, TC* uc, const int* done, cudaStream_t st, int kind) {            \
     if (T.rf_state != 1) throw Error(AMG_ERR_INVALID_ARG, "internal: restriction operator R not built"); \
+    TC* u2 = smooth_next ? uc : nullptr;                                                               \
+    const TC* dc = smooth_next ? dinvs<TC>(C) : nullptr;                                               \
     dispatch_k(K, [&](auto kc) {                                                                       \
       constexpr int KK = decltype(kc)::value;                                                          \
-      auto go = [&](auto kern) {                                                                       \
-        const int grid = resident_grid(kern, ((long long)T.nagg + NWARP - 1) / NWARP);                 \
-        kern<<<grid, BS, 0, st>>>(T.nagg, T.rf_ptr, T.rf_col, rfvals<TC>(T), T.coarse_start, f, fc,     \
-                                  smooth_next ? uc : nullptr, smooth_next ? dinvs<TC>(C) : nullptr,    \
-                                  done);                                                               \
-      };                                                                                               \
-      if (T.rf_rs == 4) go(k_restrict_rf<TC, KK, 4>);                                                  \
-      else go(k_restrict_rf<TC, KK, 8>);                                                               \
+      if (kind == 2) {                                                                                 \
+        constexpr int SPW = 32 / VT<TC, KK>::CL;                                                       \
+        auto go = [&](auto kern) {                                                                     \
+          const long long passes = ((long long)T.nagg + SPW - 1) / SPW;                                \
+          const int grid = resident_grid(kern, (passes + NWARP - 1) / NWARP);                          \
+          kern<<<grid, BS, 0, st>>>(T.nagg, T.rf_zero, T.rf_ptr, T.rf_col, rfvals<TC>(T), T.coarse_start, \
+                                    f, fc, u2, dc, nullptr, done);                                     \
+        };                                                                                             \
+        if (T.rf_rs == 4) go(k_group_rs<TC, KK, 4, 0>);                                                \
+        else go(k_group_rs<TC, KK, 8, 0>);                                                             \
+      } else {                                                                                         \
+        auto go = [&](auto kern) {                                                                     \
+          const int grid = resident_grid(kern, ((long long)T.nagg + NWARP - 1) / NWARP);               \
+          kern<<<grid, BS, 0, st>>>(T.nagg, T.rf_ptr, T.rf_col, rfvals<TC>(T), T.coarse_start, f, fc,   \
+                                    u2, dc, nullptr, done);                                            \
+        };                                                                                             \
+        if (T.rf_rs == 4) go(k_group_rf<TC, KK, 4, 0>);                                                \
+        else go(k_group_rf<TC, KK, 8, 0>);                                                             \
+      }                                                                                                \
     });                                                                                                \
     AMG_LAUNCH_CHECK();                                                                                \
   }                                                                                                    \

@@ -839,11 +839,15 @@ static const long long kTargets[] = {256, 512, 1024, 2048, 4096, 8192};
 
 // AMG_COARSE_KERNELS in the environment overrides the tuner on grouped
 // coarse levels: "grouped" takes the grouped sweep and restriction wherever
-// the level allows them, "csr" never takes them; unset, timing decides.
+// the level allows them (timing picks among their forms), "groupwarp" and
+// "groupslot" also fix the sweep to one warp or one slot of lanes per row
+// group, "csr" never takes them; unset, timing decides.
 static int coarse_kernel_override() {
   const char* e = std::getenv("AMG_COARSE_KERNELS");
   if (!e) return 0;
   if (std::strcmp(e, "grouped") == 0) return 1;
+  if (std::strcmp(e, "groupwarp") == 0) return 2;
+  if (std::strcmp(e, "groupslot") == 0) return 3;
   if (std::strcmp(e, "csr") == 0) return -1;
   return 0;
 }
@@ -870,10 +874,15 @@ static std::vector<int> nzl_candidates(int K) {
 // ------------------------------------------------- tuned choices, applied --
 // Each tuner ends by applying its choice through these, and a choice read
 // back from the tuning cache takes the same path.
+static void ensure_gw(Plan& P, int k);
 static void apply_level(Plan& P, Workspace& W, int k, long long target, int stage, int nzl) {
   std::vector<int> sys = (k == 0) ? P.h_sys_row : std::vector<int>{0, P.lev[k].n};
   W.rp[k] = make_rpart(W.ar, P.lev[k], target, sys, W.err);
   W.rp[k].sg.enabled = W.rp[k].sg.enabled && stage;
+  if (nzl == NZL_GROUP_WARP || nzl == NZL_GROUP_SLOT) {
+    ensure_gw(P, k);
+    if (P.lev[k].gw_state != 1) nzl = 0;
+  }
   W.nzl[k] = nzl;
   W.t_rp[k] = target;
   W.t_rps[k] = stage;
@@ -891,9 +900,10 @@ static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, 
   W.tp[k].jl = 1 << ((warp / 8) % 4);  // grouped restriction: lanes per group column split
   // restriction by R (one pre-sweep): replaces the restriction kernel above
   // in the V-cycle; the variant cycles keep the CSR restriction
-  int rf = (warp / 32) % 2;
+  int rf = (warp / 32) % 4;  // 1: R by a warp per aggregate, 2: by a slot per aggregate
   const int rov = rform_override();
-  if (rov != 0) rf = rov > 0 ? 1 : 0;
+  if (rov < 0) rf = 0;
+  if (rov > 0) rf = rov;
   if (rf && W.pre == 1) ensure_rform(P, k);
   if (P.tr[k].rf_state != 1 || W.pre != 1) rf = 0;
   if ((int)W.rform.size() < P.L - 1) W.rform.assign(std::max(P.L - 1, 0), 0);
@@ -1046,6 +1056,26 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
       AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       if (tune_log()) fprintf(stderr, "[tune] level %d K %d smooth grouped jl %d: %.1f us\n", k, K, jl, ms * 1e3 / 3);
       if (ms < gbest) {
+        gbest = ms;
+        gn = code;
+      }
+    }
+    ensure_gw(P, k);
+    // one warp per row group, or one slot of lanes per row group
+    for (int code : {NZL_GROUP_WARP, NZL_GROUP_SLOT}) {
+      if (P.lev[k].gw_state != 1) break;
+      launch_smooth<TC>(K, code, L, W.rp[k], f, u, v, W.zero_flag, 0);
+      AMG_CUDA(cudaEventRecord(e0, 0));
+      for (int r = 0; r < 3; ++r) launch_smooth<TC>(K, code, L, W.rp[k], f, u, v, W.zero_flag, 0);
+      AMG_CUDA(cudaEventRecord(e1, 0));
+      AMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (tune_log())
+        fprintf(stderr, "[tune] level %d K %d smooth grouped, %s per group: %.1f us\n", k, K,
+                code == NZL_GROUP_WARP ? "warp" : "slot", ms * 1e3 / 3);
+      const bool forced = (ovr == 2 && code == NZL_GROUP_WARP) || (ovr == 3 && code == NZL_GROUP_SLOT);
+      if ((ms < gbest && ovr < 2) || forced) {
         gbest = ms;
         gn = code;
       }
@@ -1237,11 +1267,12 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
       tc.pwarp = (code / 4) % 2;
       tc.jl = 1 << ((code / 8) % 4);
       const bool nxt = k + 1 < P.L - 1;
-      auto run_rf = [&] {
-        launch_restrict_rf<TC>(K, P.tr[k], P.lev[k + 1], nxt, static_cast<TC*>(W.f[k]),
-                               static_cast<TC*>(W.f[k + 1]), static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0);
-      };
-      auto time_rf = [&](int reps) {
+      auto time_rf = [&](int kind, int reps) {
+        auto run_rf = [&] {
+          launch_restrict_rf<TC>(K, P.tr[k], P.lev[k + 1], nxt, static_cast<TC*>(W.f[k]),
+                                 static_cast<TC*>(W.f[k + 1]), static_cast<TC*>(W.v[k + 1]), W.zero_flag, 0,
+                                 kind);
+        };
         run_rf();
         AMG_CUDA(cudaEventRecord(e0, 0));
         for (int r = 0; r < reps; ++r) run_rf();
@@ -1251,15 +1282,16 @@ static void tune_transfer(Plan& P, Workspace& W, int k) {
         AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         return ms / reps;
       };
-      float mc = 1e30f, mr = 1e30f;
+      float mc = 1e30f, mr = 1e30f, ms2 = 1e30f;
       for (int round = 0; round < 3; ++round) {
         mc = std::min(mc, time_tp(tc, 5));
-        mr = std::min(mr, time_rf(5));
+        mr = std::min(mr, time_rf(1, 5));
+        ms2 = std::min(ms2, time_rf(2, 5));
       }
       if (tune_log())
-        fprintf(stderr, "[tune] level %d K %d restrict by R: %.1f us against %.1f us\n", k, K, mr * 1e3,
-                mc * 1e3);
-      rf = mr < mc ? 1 : 0;
+        fprintf(stderr, "[tune] level %d K %d restrict by R: warp %.1f us, slot %.1f us, against %.1f us\n", k, K,
+                mr * 1e3, ms2 * 1e3, mc * 1e3);
+      if (std::min(mr, ms2) < mc) rf = ms2 < mr ? 2 : 1;
       AMG_CUDA(cudaDeviceSynchronize());
     }
   }
@@ -1635,8 +1667,10 @@ static void ensure_rform(Plan& P, int k) {
     std::sort(halo.begin(), halo.end());
     halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
     const size_t base = pcol.size();
-    if (base + halo.size() >= (size_t)INT32_MAX - 64) return;
+    if (base + halo.size() + RF_PAD >= (size_t)INT32_MAX - 64) return;
     pcol.insert(pcol.end(), halo.begin(), halo.end());
+    // padded to a multiple of RF_PAD entries: a valid column, zero values
+    while ((pcol.size() - base) % RF_PAD) pcol.push_back(halo[0]);
     pval.resize(pcol.size() * RS, 0.0);
     double* V = pval.data() + base * RS;
     auto pos = [&](int h) { return (size_t)(std::lower_bound(halo.begin(), halo.end(), h) - halo.begin()); };
@@ -1652,7 +1686,7 @@ static void ensure_rform(Plan& P, int k) {
       }
     ptr[a + 1] = (int)pcol.size();
   }
-  const size_t ne = pcol.size();
+  const size_t ne = pcol.size();  // a multiple of RF_PAD; the zero batch follows
   pcol.resize(ne + 16, 0);
   pval.resize((ne + 16) * RS, 0.0);
   std::vector<float> pv32(pval.size());
@@ -1667,16 +1701,72 @@ static void ensure_rform(Plan& P, int k) {
   AMG_CUDA(cudaMemcpy(T.rf_v32, pv32.data(), pv32.size() * sizeof(float), cudaMemcpyHostToDevice));
   T.rf_rs = RS;
   T.rf_entries = (long long)ne;
+  T.rf_zero = (int)ne;
   T.rf_state = 1;
+}
+
+// Entry-major copy of grouped level k for the warp-per-group sweep: one warp
+// per row group copies the group's pattern (its first row's columns) and,
+// per entry, the values of its rows, padded with zeros to rs.
+__global__ void k_build_gw(int ngrp, const int* __restrict__ gstart, const int* __restrict__ rowptr,
+                           const int* __restrict__ col, const double* __restrict__ val, const int* __restrict__ gptr,
+                           int rs, int* __restrict__ gcol, double* __restrict__ g64, float* __restrict__ g32) {
+  const int g = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (g >= ngrp) return;
+  const int r0 = gstart[g], ra = gstart[g + 1] - r0, b = rowptr[r0], S = rowptr[r0 + 1] - b, e = gptr[g];
+  const int Sp = gptr[g + 1] - e;  // padded: a valid column with zero values
+  for (int jj = lane; jj < Sp; jj += 32) {
+    gcol[e + jj] = col[b + (jj < S ? jj : 0)];
+    for (int p = 0; p < rs; ++p) {
+      const double v = (p < ra && jj < S) ? val[rowptr[r0 + p] + jj] : 0.0;
+      g64[(size_t)(e + jj) * rs + p] = v;
+      g32[(size_t)(e + jj) * rs + p] = (float)v;
+    }
+  }
+}
+
+static void ensure_gw(Plan& P, int k) {
+  Level& L = P.lev[k];
+  if (L.gw_state != 0) return;
+  L.gw_state = -1;
+  if (k < 1 || !L.grp_ok || L.grp_rmax < 1 || L.grp_rmax > 8 || !L.val64) return;
+  const std::vector<int>& gs = P.tr[k - 1].h_coarse_start;
+  if ((int)gs.size() != L.ngrp + 1 || (int)L.h_rowptr.size() != L.n + 1) return;
+  std::vector<int> ptr(L.ngrp + 1, 0);
+  for (int g = 0; g < L.ngrp; ++g) {
+    const long long S = (long long)L.h_rowptr[gs[g] + 1] - L.h_rowptr[gs[g]];
+    const long long Sp = (S + RF_PAD - 1) / RF_PAD * RF_PAD;  // padded pattern
+    if (S < 1 || (long long)ptr[g] + Sp >= (long long)INT32_MAX - 64) return;
+    ptr[g + 1] = ptr[g] + (int)Sp;
+  }
+  const int rs = L.grp_rmax <= 4 ? 4 : 8;
+  const size_t ne = (size_t)ptr[L.ngrp] + 16;
+  L.gw_ptr = P.arena->alloc<int>(ptr.size());
+  L.gw_col = P.arena->alloc<int>(ne);
+  L.gw_v64 = P.arena->alloc<double>(ne * rs);
+  L.gw_v32 = P.arena->alloc<float>(ne * rs);
+  AMG_CUDA(cudaDeviceSynchronize());
+  AMG_CUDA(cudaMemcpy(L.gw_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  AMG_CUDA(cudaMemset(L.gw_col, 0, ne * sizeof(int)));
+  AMG_CUDA(cudaMemset(L.gw_v64, 0, ne * rs * sizeof(double)));
+  AMG_CUDA(cudaMemset(L.gw_v32, 0, ne * rs * sizeof(float)));
+  k_build_gw<<<(L.ngrp + 7) / 8, 256>>>(L.ngrp, L.gstart, L.rowptr, L.col, L.val64, L.gw_ptr, rs, L.gw_col,
+                                        L.gw_v64, L.gw_v32);
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA(cudaDeviceSynchronize());
+  L.gw_rs = rs;
+  L.gw_zero = ptr[L.ngrp];
+  L.gw_state = 1;
 }
 
 // AMG_RESTRICT_RFORM in the environment overrides the tuner's choice of the
 // restriction by R = P^T (I - A D^{-1}) (one pre-sweep only): "1" takes it on
-// every transfer that has it, "0" never; unset, timing decides.
+// every transfer that has it with a warp per aggregate, "2" with a slot of
+// lanes per aggregate, "0" never; unset, timing decides.
 static int rform_override() {
   const char* e = std::getenv("AMG_RESTRICT_RFORM");
   if (!e || !*e) return 0;
-  return e[0] == '1' ? 1 : (e[0] == '0' ? -1 : 0);
+  return e[0] == '1' ? 1 : (e[0] == '2' ? 2 : (e[0] == '0' ? -1 : 0));
 }
 
 static void make_var(Plan& P, Workspace& W, int variant);
@@ -2057,7 +2147,8 @@ static void enqueue_cycle(amg_hierarchy* h, Plan& P, Workspace& W, cudaStream_t 
       P.tr[k].rf_last = by_r ? 1 : 0;
       if (by_r) {
         // fc = R f: the iterate entering the restriction is D^{-1} f
-        launch_restrict_rf<TC>(K, P.tr[k], P.lev[k + 1], smooth_next, F(k), F(k + 1), cur[k + 1], done, st);
+        launch_restrict_rf<TC>(K, P.tr[k], P.lev[k + 1], smooth_next, F(k), F(k + 1), cur[k + 1], done, st,
+                               W.rform[k]);
       } else if (k == 0 && W.u0free) {
         // t = f - A D^{-1} f: the first pre-sweep from zero is folded into the
         // column-scaled matrix, so u0 = D^{-1} f is never stored

@@ -104,3 +104,57 @@ def test_grouped_fp32_cycle(amg, problems, monkeypatch, tmp_path, name):
     assert tr.max() <= 1.1e-8, tr.max()
     for c in range(k):
         assert i32[c]["iters"] <= i64[c]["iters"] + 3, (c, i32[c]["iters"], i64[c]["iters"])
+
+
+SWEEP_CODE = {"groupwarp": -16, "groupslot": -17}
+
+
+@pytest.mark.parametrize("mode", list(SWEEP_CODE))
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("k", [8, 32])
+def test_group_warp_sweep_fp64_matches_oracle(amg, problems, monkeypatch, tmp_path, name, k, mode):
+    """The sweep with one warp, or one slot of lanes, per row group (an
+    entry-major copy of the level's values, patterns padded to multiples of
+    8 entries, each pattern row of u gathered once per group)."""
+    P, Ho = problems[name]
+    B = np.random.default_rng(40 + k).uniform(-1.0, 1.0, (P.n, k))
+    Xg, ig, st, nzl, kern = _solve(amg, monkeypatch, tmp_path, P, mode, B)
+    assert st == amg.AMG_OK
+    assert all(n == SWEEP_CODE[mode] for n in nzl[1:]), nzl
+    for c in (0, k // 2, k - 1):
+        _, res = O.solve(Ho, B[:, c])
+        assert abs(ig[c]["iters"] - res[0].iters) <= 1, (c, ig[c]["iters"], res[0].iters)
+        xf, _ = O.solve(Ho, B[:, c], fixed_iters=ig[c]["iters"])
+        assert np.linalg.norm(Xg[:, c] - xf) / np.linalg.norm(xf) <= 1e-10
+
+
+@pytest.mark.parametrize("mode", list(SWEEP_CODE))
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_group_warp_sweep_fp32_cycle(amg, problems, monkeypatch, tmp_path, name, mode):
+    P, Ho = problems[name]
+    k = 32
+    B = np.random.default_rng(6).uniform(-1.0, 1.0, (P.n, k))
+    X64, i64, st64, _, _ = _solve(amg, monkeypatch, tmp_path, P, mode, B)
+    X32, i32, st32, nzl, kern = _solve(amg, monkeypatch, tmp_path, P, mode, B, cycle_precision=32)
+    assert st64 == amg.AMG_OK and st32 == amg.AMG_OK
+    assert all(n == SWEEP_CODE[mode] for n in nzl[1:]), nzl
+    tr = np.linalg.norm(B - P.A @ X32, axis=0) / np.linalg.norm(B, axis=0)
+    assert tr.max() <= 1.1e-8, tr.max()
+    for c in range(k):
+        assert i32[c]["iters"] <= i64[c]["iters"] + 3, (c, i32[c]["iters"], i64[c]["iters"])
+
+
+@pytest.mark.parametrize("mode", list(SWEEP_CODE))
+def test_group_warp_sweep_vcycle(amg, problems, monkeypatch, tmp_path, mode):
+    """One float64 V-cycle with the warp- or slot-per-group sweep on every
+    coarse level against the oracle's, element by element."""
+    P, Ho = problems["aniso64"]
+    R = np.random.default_rng(8).uniform(-1.0, 1.0, (P.n, 16))
+    monkeypatch.setenv("AMG_COARSE_KERNELS", mode)
+    monkeypatch.setenv("AMG_FUSED_COARSE", "0")
+    monkeypatch.setenv("AMG_TUNE_CACHE", str(tmp_path / "tune_vc.txt"))
+    H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
+    Z = H.vcycle(R)
+    H.close()
+    Zo = O.vcycle(Ho, R)
+    assert np.abs(Z - Zo).max() <= 1e-12 * np.abs(Zo).max()

@@ -5,8 +5,10 @@ restriction of Section 5's V-cycle is u = D^{-1} f, so the restricted
 residual P^T (f - A u) equals R f.  The library keeps R by aggregate (every
 coarse dof of an aggregate has the same column pattern, the rows that the
 aggregate's rows of A reach) and applies it as a grouped product that
-gathers each of those rows once.  AMG_RESTRICT_RFORM=1 makes every transfer
-take it, =0 none.  These tests force each choice and check, against the FP64
+gathers each of those rows once, either with a warp per aggregate or with a
+slot of lanes per aggregate (patterns padded to multiples of 8 entries).
+AMG_RESTRICT_RFORM=1 (warp) or =2 (slot) makes every transfer take it, =0
+none.  These tests force each choice and check, against the FP64
 oracle: one V-cycle element by element; PCG iteration counts within one and
 the iterate at the GPU's count within 1e-10; the float32 cycle (both CG
 forms) to the same true residual within three extra iterations; a batch of
@@ -59,12 +61,13 @@ def _by_r(H):
     return [H.restriction_info(k) for k in range(L - 1)]
 
 
+@pytest.mark.parametrize("form", ["1", "2"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("k", [1, 8, 32])
-def test_rform_vcycle_fp64_matches_oracle(amg, problems, monkeypatch, name, k):
+def test_rform_vcycle_fp64_matches_oracle(amg, problems, monkeypatch, name, k, form):
     P, Ho = problems[name]
     R = np.random.default_rng(100 + k).uniform(-1.0, 1.0, (P.n, k))
-    H = _hier(amg, monkeypatch, P, "1")
+    H = _hier(amg, monkeypatch, P, form)
     Z = H.vcycle(R if k > 1 else R[:, 0])
     info = _by_r(H)
     H.close()
@@ -89,12 +92,13 @@ def test_rform_off_takes_csr(amg, problems, monkeypatch, name):
     assert np.abs(Z - Zo).max() <= 1e-12 * np.abs(Zo).max()
 
 
+@pytest.mark.parametrize("form", ["1", "2"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
-def test_rform_pcg_fp64_matches_oracle(amg, problems, monkeypatch, name):
+def test_rform_pcg_fp64_matches_oracle(amg, problems, monkeypatch, name, form):
     P, Ho = problems[name]
     k = 8
     B = np.random.default_rng(11).uniform(-1.0, 1.0, (P.n, k))
-    H = _hier(amg, monkeypatch, P, "1")
+    H = _hier(amg, monkeypatch, P, form)
     X, inf, st = H.solve(B)
     info = _by_r(H)
     H.close()
@@ -107,13 +111,14 @@ def test_rform_pcg_fp64_matches_oracle(amg, problems, monkeypatch, name):
         assert np.linalg.norm(X[:, c] - xf) / np.linalg.norm(xf) <= 1e-10
 
 
+@pytest.mark.parametrize("form", ["1", "2"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("outer", [0, 1])
-def test_rform_fp32_cycle(amg, problems, monkeypatch, name, outer):
+def test_rform_fp32_cycle(amg, problems, monkeypatch, name, outer, form):
     P, Ho = problems[name]
     k = 32
     B = np.random.default_rng(5).uniform(-1.0, 1.0, (P.n, k))
-    H = _hier(amg, monkeypatch, P, "1")
+    H = _hier(amg, monkeypatch, P, form)
     X64, i64, st64 = H.solve(B)
     X32, i32, st32 = H.solve(B, options=amg.opts(cycle_precision=32, outer_fp64=outer))
     info = _by_r(H)
@@ -126,11 +131,12 @@ def test_rform_fp32_cycle(amg, problems, monkeypatch, name, outer):
         assert i32[c]["iters"] <= i64[c]["iters"] + 3, (c, i32[c]["iters"], i64[c]["iters"])
 
 
-def test_rform_uneven_batch(amg, monkeypatch):
+@pytest.mark.parametrize("form", ["1", "2"])
+def test_rform_uneven_batch(amg, monkeypatch, form):
     """Two elasticity grids of different sizes in one launch sequence: each
     system's float64 iterate matches the oracle at the GPU's count."""
     Ps = [inputs.elasticity_grid(n, nrhs=1, levels=3) for n in (5, 7)]
-    monkeypatch.setenv("AMG_RESTRICT_RFORM", "1")
+    monkeypatch.setenv("AMG_RESTRICT_RFORM", form)
     monkeypatch.setenv("AMG_FUSED_COARSE", "0")
     monkeypatch.delenv("AMG_TUNE_CACHE", raising=False)
     Hs = [amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W) for P in Ps]
