@@ -839,9 +839,10 @@ static const long long kTargets[] = {256, 512, 1024, 2048, 4096, 8192};
 
 // AMG_COARSE_KERNELS in the environment overrides the tuner on grouped
 // coarse levels: "grouped" takes the grouped sweep and restriction wherever
-// the level allows them (timing picks among their forms), "groupwarp" and
-// "groupslot" also fix the sweep to one warp or one slot of lanes per row
-// group, "csr" never takes them; unset, timing decides.
+// the level allows them (the staged sweep with one CTA per 32 row groups,
+// timing picking its lane split), "groupwarp" and "groupslot" fix the sweep
+// to one warp or one slot of lanes per row group, "csr" never takes them;
+// unset, timing decides among all.
 static int coarse_kernel_override() {
   const char* e = std::getenv("AMG_COARSE_KERNELS");
   if (!e) return 0;
@@ -1060,10 +1061,11 @@ static void tune_level(Plan& P, Workspace& W, int k, const std::vector<int>& sys
         gn = code;
       }
     }
-    ensure_gw(P, k);
-    // one warp per row group, or one slot of lanes per row group
+    // one warp per row group, or one slot of lanes per row group (not under
+    // "grouped", which keeps the staged CTA-per-groups sweep)
+    if (ovr != 1) ensure_gw(P, k);
     for (int code : {NZL_GROUP_WARP, NZL_GROUP_SLOT}) {
-      if (P.lev[k].gw_state != 1) break;
+      if (ovr == 1 || P.lev[k].gw_state != 1) break;
       launch_smooth<TC>(K, code, L, W.rp[k], f, u, v, W.zero_flag, 0);
       AMG_CUDA(cudaEventRecord(e0, 0));
       for (int r = 0; r < 3; ++r) launch_smooth<TC>(K, code, L, W.rp[k], f, u, v, W.zero_flag, 0);

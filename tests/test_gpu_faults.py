@@ -32,6 +32,7 @@ def test_staged_copy_wait_gives_up_with_timeout(amg, monkeypatch):
     o = amg.opts(cycle_precision=32, maxit=500)
     monkeypatch.setenv("AMG_TEST_FIRST_WAIT", "1")
     monkeypatch.setenv("AMG_COARSE_KERNELS", "grouped")   # the grouped levels always stage
+    monkeypatch.setenv("AMG_RESTRICT_RFORM", "0")         # ... and restrict through P^T
     monkeypatch.setenv("AMG_FUSED_COARSE", "0")           # ... when they run as kernels of their own
     H = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
     with pytest.raises(amg.AMGError) as e:
@@ -42,6 +43,7 @@ def test_staged_copy_wait_gives_up_with_timeout(amg, monkeypatch):
     monkeypatch.delenv("AMG_TEST_FIRST_WAIT")
     monkeypatch.delenv("AMG_COARSE_KERNELS")
     monkeypatch.delenv("AMG_FUSED_COARSE")
+    monkeypatch.delenv("AMG_RESTRICT_RFORM")
     H2 = amg.Hierarchy(P.A, P.aggs, P.n_nodes, P.W)
     X, infos, st = H2.solve(Bd, torch.zeros_like(Bd), o)
     assert st == amg.AMG_OK
