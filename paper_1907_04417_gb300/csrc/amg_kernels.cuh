@@ -513,6 +513,13 @@ __device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c) {
   return r;
 }
 __device__ __forceinline__ F2 f2_neg(F2 a) { return F2{a.v ^ 0x8000000080000000ull}; }
+// df_norm on a pair of columns (the same steps as the scalar form)
+__device__ __forceinline__ void df_norm_x2(F2& sh, F2& sl) {
+  const F2 s = f2_add(sh, sl);
+  const F2 e = f2_sub(sl, f2_sub(s, sh));
+  sh = s;
+  sl = e;
+}
 // df_acc1 on a pair of columns (the same steps as the scalar form)
 __device__ __forceinline__ void df_acc1_x2(F2 ah, F2 al, F2 x, F2& sh, F2& sl) {
   const F2 p = f2_mul(ah, x);

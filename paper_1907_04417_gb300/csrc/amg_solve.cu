@@ -50,7 +50,7 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
 // one non-zero ahead), and the p.q accumulators live in shared memory, one
 // slot per thread, so that three CTAs fit on an SM.  Offsets into the n x K
 // blocks are 32-bit (n K < 2^32 is checked on the host).
-template <int K, int NZL, bool STG>
+template <int K, int NZL, bool STG, int UQ = 0>
 __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
                                                    const float* __restrict__ alo, const float* p0,
@@ -63,11 +63,21 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
   __shared__ double sm[BS];
   __shared__ double tot[64];
   constexpr int CPT = VT<float, K>::CPT, CL = VT<float, K>::CL, G = NZL * CL, RPW = 32 / G;
-  __shared__ float sdot[2 * CPT][BS];
+  // the packed path: batches of full rows, column pairs (p.q accumulated on
+  // pairs too, in sdot2); UQ, when set, is the batch (the longest row)
+  constexpr bool PK = gather_depth<NZL>() != 4 && CPT % 2 == 0;
+  constexpr int UB = UQ > 0 ? UQ : gather_depth<NZL>(), NQ = PK ? CPT / 2 : 1;
+  __shared__ float sdot[PK ? 1 : 2 * CPT][BS];
+  __shared__ F2 sdot2[2 * NQ][PK ? BS : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / G, lg = lane % G, nzl = lg / CL, cl = lg % CL;
+  if constexpr (PK) {
 #pragma unroll
-  for (int t = 0; t < 2 * CPT; ++t) sdot[t][threadIdx.x] = 0.f;
+    for (int q = 0; q < 2 * NQ; ++q) sdot2[q][threadIdx.x] = F2{0ull};
+  } else {
+#pragma unroll
+    for (int t = 0; t < 2 * CPT; ++t) sdot[t][threadIdx.x] = 0.f;
+  }
   // row chunks: one per CTA, or (persistent launch) every gridDim.x-th
   // chunk; staged launches take col, val_hi and val_lo (and rowptr) through
   // the double-buffered pipeline, the next chunk arriving while this one is
@@ -109,11 +119,11 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
     if (valid) {
       const int j1 = rp[i + 1 - roff] - joff;
       int j = rp[i - roff] - joff + nzl;
-      if constexpr (gather_depth<NZL>() != 4 && CPT % 2 == 0) {
+      if constexpr (PK) {
         // predicated batches: every gather of a batch is issued before the
         // first product (a 9-point row in one memory round trip); the
         // double-float steps run on column pairs
-        constexpr int U = gather_depth<NZL>(), NP = CPT / 2;
+        constexpr int U = UB, NP = CPT / 2;
         F2 h2[NP], l2[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) h2[q] = l2[q] = F2{0ull};
@@ -148,12 +158,13 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
+          df_norm_x2(h2[q], l2[q]);
           f2_unpack(h2[q], sh[2 * q], sh[2 * q + 1]);
           f2_unpack(l2[q], sl[2 * q], sl[2 * q + 1]);
         }
       } else if constexpr (gather_depth<NZL>() != 4) {
         // predicated batches, scalar columns
-        constexpr int U = gather_depth<NZL>();
+        constexpr int U = UB;
         for (; j < j1; j += U * NZL) {
           float xv[U][CPT];
 #pragma unroll
@@ -192,8 +203,10 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
 #pragma unroll
         for (int t = 0; t < CPT; ++t) df_acc1(a, b, xv[t], sh[t], sl[t]);
       }
+      if constexpr (!PK) {  // (the packed path renormalised its pairs)
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) df_norm(sh[t], sl[t]);
+        for (int t = 0; t < CPT; ++t) df_norm(sh[t], sl[t]);
+      }
     }
     if constexpr (NZL > 1) {
 #pragma unroll
@@ -210,20 +223,42 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
       ldv<float, CPT>(p + o, pv);
       stv<float, CPT>(qh + o, sh);
       stv<float, CPT>(ql + o, sl);
+      if constexpr (PK) {
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) {
-        float h = sdot[t][threadIdx.x], l = sdot[CPT + t][threadIdx.x];
-        df_acc1(sh[t], sl[t], pv[t], h, l);
-        sdot[t][threadIdx.x] = h;
-        sdot[CPT + t][threadIdx.x] = l;
+        for (int q = 0; q < NQ; ++q) {
+          F2 h = sdot2[q][threadIdx.x], l = sdot2[NQ + q][threadIdx.x];
+          df_acc1_x2(f2_pack(sh[2 * q], sh[2 * q + 1]), f2_pack(sl[2 * q], sl[2 * q + 1]),
+                     f2_pack(pv[2 * q], pv[2 * q + 1]), h, l);
+          sdot2[q][threadIdx.x] = h;
+          sdot2[NQ + q][threadIdx.x] = l;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) {
+          float h = sdot[t][threadIdx.x], l = sdot[CPT + t][threadIdx.x];
+          df_acc1(sh[t], sl[t], pv[t], h, l);
+          sdot[t][threadIdx.x] = h;
+          sdot[CPT + t][threadIdx.x] = l;
+        }
       }
     }
   }
   if (STG && sg.enabled) __syncthreads();  // the buffer is refilled two chunks on
   }
   double d[CPT];
+  if constexpr (PK) {
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) d[t] = (double)sdot[t][threadIdx.x] + (double)sdot[CPT + t][threadIdx.x];
+    for (int q = 0; q < NQ; ++q) {
+      float h0, h1, l0, l1;
+      f2_unpack(sdot2[q][threadIdx.x], h0, h1);
+      f2_unpack(sdot2[NQ + q][threadIdx.x], l0, l1);
+      d[2 * q] = (double)h0 + (double)l0;
+      d[2 * q + 1] = (double)h1 + (double)l1;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) d[t] = (double)sdot[t][threadIdx.x] + (double)sdot[CPT + t][threadIdx.x];
+  }
   cta_colsum<K, CPT>(d, sm, ks.partial + (size_t)blockIdx.x * K);
   if (!arrive_two_level(ks, RED_Q, K, sm, tot)) return;
   finish_alpha<K>(ks, sm, tot);
@@ -2258,7 +2293,12 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
       dispatch_nzl(W.K, W.nzl_q, [&](auto nc) {
         constexpr int NZ = decltype(nc)::value;
         if constexpr (VT<float, KK>::CL * NZ <= 32) {
-          auto kern = W.q_stage && W.rq.sg.enabled ? k_cg_q_df<KK, NZ, true> : k_cg_q_df<KK, NZ, false>;
+          // a batch of 9 when every row has at most 9 entries (a 9-point row
+          // then wastes no predicated step)
+          const bool b9 = NZ == 1 && L.max_row_len <= 9;
+          const bool stg = W.q_stage && W.rq.sg.enabled;
+          auto kern = stg ? (b9 ? k_cg_q_df<KK, NZ, true, 9> : k_cg_q_df<KK, NZ, true>)
+                          : (b9 ? k_cg_q_df<KK, NZ, false, 9> : k_cg_q_df<KK, NZ, false>);
           Stage sg = W.rq.sg;
           sg.enabled = sg.enabled && W.q_stage;
           size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
