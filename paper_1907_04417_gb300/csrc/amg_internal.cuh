@@ -106,6 +106,7 @@ struct Level {
   float* val32 = nullptr;
   float* vallo = nullptr;    // level 0: val64 - val32 (the low half of a double-float)
   float* val_sc = nullptr;   // level 0: fl32(a_ij / d_j), A D^{-1} for the u0-free float32 cycle
+  float2* hl = nullptr;      // level 0: (val32, vallo) per non-zero (the paired q = A p), on first use
   double* dinv64 = nullptr;  // 1 / sum_j |a_ij|   (non-coarsest levels)
   float* dinv32 = nullptr;
   int max_row_len = 0;

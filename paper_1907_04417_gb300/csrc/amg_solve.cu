@@ -50,12 +50,15 @@ __device__ __forceinline__ void finish_alpha(KState& ks, double* sm, double* tot
 // one non-zero ahead), and the p.q accumulators live in shared memory, one
 // slot per thread, so that three CTAs fit on an SM.  Offsets into the n x K
 // blocks are 32-bit (n K < 2^32 is checked on the host).
-template <int K, int NZL, bool STG, int UQ = 0>
+// PKD: val_hi and val_lo of a non-zero come as one 8-byte pair of hl (one
+// load instead of two; the unstaged path only).
+template <int K, int NZL, bool STG, int UQ = 0, bool PKD = false>
 __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                                    const int* __restrict__ col, const float* __restrict__ ahi,
                                                    const float* __restrict__ alo, const float* p0,
                                                    const float* p1, float* __restrict__ qh,
-                                                   float* __restrict__ ql, KState ks, Stage sg, int nchunk) {
+                                                   float* __restrict__ ql, KState ks, Stage sg, int nchunk,
+                                                   const float2* __restrict__ hl) {
   if (*ks.done) return;
   // p_k lives in p0 for even k, in p1 for odd k (k the device iteration counter)
   const float* __restrict__ p = (*ks.iter & 1) ? p1 : p0;
@@ -129,6 +132,36 @@ __global__ void __launch_bounds__(BS, 3) k_cg_q_df(const int* __restrict__ cta_r
         for (int q = 0; q < NP; ++q) h2[q] = l2[q] = F2{0ull};
         for (; j < j1; j += U * NZL) {
           F2 xv[U][NP];
+          if constexpr (PKD) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int jj = j + u * NZL;
+              if (jj < j1) {
+                const float* src = p + (unsigned)cc[jj] * (unsigned)K + lo;
+                if constexpr (NP == 2) {
+                  const ulonglong2 t2 = __ldg(reinterpret_cast<const ulonglong2*>(src));
+                  xv[u][0] = F2{t2.x};
+                  xv[u][1] = F2{t2.y};
+                } else {
+#pragma unroll
+                  for (int q = 0; q < NP; ++q)
+                    xv[u][q] = F2{__ldg(reinterpret_cast<const unsigned long long*>(src) + q)};
+                }
+              } else {
+#pragma unroll
+                for (int q = 0; q < NP; ++q) xv[u][q] = F2{0ull};
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const int jj = j + u * NZL;
+              const float2 ab = jj < j1 ? __ldg(hl + jj) : make_float2(0.f, 0.f);
+              const F2 a2 = f2_pack(ab.x, ab.x), b2 = f2_pack(ab.y, ab.y);
+#pragma unroll
+              for (int q = 0; q < NP; ++q) df_acc1_x2(a2, b2, xv[u][q], h2[q], l2[q]);
+            }
+            continue;
+          }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int jj = j + u * NZL;
@@ -675,6 +708,7 @@ struct Workspace {
   std::vector<int> nzl;   // per level
   int nzl_q = 0;          // lanes per row of the level-0 q = A p
   int q_stage = 1;        // whether the double-float q = A p stages its matrix slice
+  int q_pack = 0;         // whether it reads the values as (hi, lo) pairs (unstaged)
   RPart rq{};             // level-0 row ranges of the double-float q = A p (own CTA size)
   int q_grid = 0;         // > 0: persistent q launch of q_grid CTAs over rq's ranges
   // persistent level-0 launches (one system): CTAs of the update, direction
@@ -951,9 +985,21 @@ static void apply_transfer(Plan& P, Workspace& W, int k, int target, int stage, 
 }
 static KState view_state(Arena& ar, const KState& ks, const RPart& rp, int K);
 static RPart make_flat(Arena& ar, int ncta);
+static void ensure_packed(Plan& P);
 static void apply_q(Plan& P, Workspace& W, long long target, int nzl, int stage, int grid) {
   W.nzl_q = nzl;
-  W.q_stage = stage;
+  W.q_pack = 0;
+  // AMG_Q_PAIRED=1 takes the (hi, lo) pairs (and so an unstaged launch), =0
+  // never; unset, the tuned or cached choice stands
+  const char* qp = std::getenv("AMG_Q_PAIRED");
+  if (W.split && qp && qp[0] == '1') stage = 2;
+  if (qp && qp[0] == '0' && stage == 2) stage = 0;
+  if (stage == 2) {  // (hi, lo) value pairs, unstaged
+    ensure_packed(P);
+    W.q_pack = P.lev[0].hl ? 1 : 0;
+    if (!W.q_pack) stage = 0;
+  }
+  W.q_stage = stage == 2 ? 0 : stage;
   W.q_grid = grid;
   if (target > 0) {
     W.rq = make_rpart(W.ar, P.lev[0], target, P.h_sys_row, W.err);
@@ -1446,6 +1492,25 @@ static void tune_q(Plan& P, Workspace& W) {
     W.rq = keep;
     W.ksq = keep_ks;
     apply_q(P, W, bt, bn, bs, bg);
+    // (AMG_Q_PAIRED, when set, has decided in apply_q)
+    const char* qp = std::getenv("AMG_Q_PAIRED");
+    if (bs == 0 && !(qp && *qp)) {
+      // the chosen unstaged launch against the same launch reading the
+      // values as (hi, lo) pairs, in alternating rounds
+      ensure_packed(P);
+      if (P.lev[0].hl) {
+        float mu = 1e30f, mp = 1e30f;
+        for (int round = 0; round < 3; ++round) {
+          W.q_pack = 0;
+          mu = std::min(mu, time_q("df chosen", bt, bn, 0));
+          W.q_pack = 1;
+          mp = std::min(mp, time_q("df packed", bt, bn, 2));
+        }
+        W.q_pack = 0;
+        AMG_CUDA(cudaDeviceSynchronize());
+        if (mp < mu) apply_q(P, W, bt, bn, 2, bg);
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1804,6 +1869,27 @@ static int rform_override() {
   const char* e = std::getenv("AMG_RESTRICT_RFORM");
   if (!e || !*e) return 0;
   return e[0] == '1' ? 1 : (e[0] == '2' ? 2 : (e[0] == '0' ? -1 : 0));
+}
+
+// Level 0's values as (val32, vallo) pairs for the double-float q = A p
+// (one 8-byte load per non-zero), 16 zero pairs of padding; made once per
+// plan on first use.
+__global__ void k_pack_q(long long nnz, const float* __restrict__ hi, const float* __restrict__ lo,
+                         float2* __restrict__ hl) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nnz + 16) return;
+  hl[j] = j < nnz ? make_float2(hi[j], lo[j]) : make_float2(0.f, 0.f);
+}
+
+static void ensure_packed(Plan& P) {
+  Level& L = P.lev[0];
+  if (L.hl || !L.val32 || !L.vallo || L.nnz <= 0) return;
+  AMG_CUDA(cudaDeviceSynchronize());
+  float2* hl = P.arena->alloc<float2>((size_t)L.nnz + 16);
+  k_pack_q<<<(unsigned)((L.nnz + 16 + 255) / 256), 256>>>(L.nnz, L.val32, L.vallo, hl);
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA(cudaDeviceSynchronize());
+  L.hl = hl;
 }
 
 static void make_var(Plan& P, Workspace& W, int variant);
@@ -2297,15 +2383,17 @@ static void launch_cg_q(Workspace& W, const Level& L, cudaStream_t st) {
           // then wastes no predicated step)
           const bool b9 = NZ == 1 && L.max_row_len <= 9;
           const bool stg = W.q_stage && W.rq.sg.enabled;
+          const bool pkd = W.q_pack && L.hl && !stg;
           auto kern = stg ? (b9 ? k_cg_q_df<KK, NZ, true, 9> : k_cg_q_df<KK, NZ, true>)
-                          : (b9 ? k_cg_q_df<KK, NZ, false, 9> : k_cg_q_df<KK, NZ, false>);
+                          : pkd ? (b9 ? k_cg_q_df<KK, NZ, false, 9, true> : k_cg_q_df<KK, NZ, false, 0, true>)
+                                : (b9 ? k_cg_q_df<KK, NZ, false, 9> : k_cg_q_df<KK, NZ, false>);
           Stage sg = W.rq.sg;
           sg.enabled = sg.enabled && W.q_stage;
           size_t smem = pipe_bytes(sg, 2, W.q_grid > 0 ? 2 : 1);
           ensure_smem(kern, smem);
           const int grid = W.q_grid > 0 ? W.q_grid : W.rq.ncta;
           kern<<<grid, BS, smem, st>>>(W.rq.cta_row, L.rowptr, L.col, L.val32, L.vallo, W.ph, W.ph2, W.qh, W.ql,
-                                       W.ksq, sg, W.rq.ncta);
+                                       W.ksq, sg, W.rq.ncta, L.hl);
         }
       });
     });
