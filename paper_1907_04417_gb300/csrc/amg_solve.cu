@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
 // because q = A p is formed from the same rounded p.  After the last
 // iteration k_cg_x_df applies the steps still pending.
 template <int K>
-__global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
+__global__ void __launch_bounds__(BS, 3) k_cg_p_df(const int* __restrict__ cta_row, const float* __restrict__ z,
                                                 float* p0, float* p1, float* __restrict__ xh,
                                                 float* __restrict__ xl, KState ks, int first, int nchunk) {
   if (*ks.done) return;
@@ -522,36 +522,55 @@ __global__ void __launch_bounds__(BS) k_cg_p_df(const int* __restrict__ cta_row,
     split2(ks.alpha[s * K + cfirst + t], ah[t], al[t]);
     split2(ks.alpha_prev[s * K + cfirst + t], ch[t], cl[t]);
   }
-  for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
-  const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
-  for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
-    float zv[CPT], pv[CPT];
-    ldv<float, CPT>(z + e, zv);
-    if (first) {
+  // a thread keeps the loads of UN row-column groups in flight (4 without
+  // the x step, 2 with it) before any arithmetic
+  auto pass = [&](auto unc, bool stp) {
+    constexpr int UN = decltype(unc)::value;
+    for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+      const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
+      for (size_t eb = e0 + (size_t)threadIdx.x * CPT; eb < e1; eb += (size_t)UN * BS * CPT) {
+        float zv[UN][CPT], pv[UN][CPT], po[UN][CPT], xa[UN][CPT], xb[UN][CPT];
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) pv[t] = zv[t];
-    } else {
-      ldp<float, CPT>(pin + e, pv);
-      if (step) {
-        float po[CPT], xa[CPT], xb[CPT];
-        ldp<float, CPT>(pout + e, po);   // p_{k-1}
-        ldp<float, CPT>(xh + e, xa);
-        ldp<float, CPT>(xl + e, xb);
-#pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-          df_acc1(ch[t], cl[t], po[t], xa[t], xb[t]);
-          df_acc1(ah[t], al[t], pv[t], xa[t], xb[t]);
-          df_norm(xa[t], xb[t]);
+        for (int u = 0; u < UN; ++u) {
+          const size_t e = eb + (size_t)u * BS * CPT;
+          if (e < e1) {
+            ldv<float, CPT>(z + e, zv[u]);
+            if (!first) ldp<float, CPT>(pin + e, pv[u]);
+            if (stp) {
+              ldp<float, CPT>(pout + e, po[u]);   // p_{k-1}
+              ldp<float, CPT>(xh + e, xa[u]);
+              ldp<float, CPT>(xl + e, xb[u]);
+            }
+          }
         }
-        stv<float, CPT>(xh + e, xa);
-        stv<float, CPT>(xl + e, xb);
-      }
 #pragma unroll
-      for (int t = 0; t < CPT; ++t) pv[t] = fmaf(bl[t], pv[t], fmaf(bh[t], pv[t], zv[t]));
+        for (int u = 0; u < UN; ++u) {
+          const size_t e = eb + (size_t)u * BS * CPT;
+          if (e >= e1) continue;
+          if (first) {
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) pv[u][t] = zv[u][t];
+          } else {
+            if (stp) {
+#pragma unroll
+              for (int t = 0; t < CPT; ++t) {
+                df_acc1(ch[t], cl[t], po[u][t], xa[u][t], xb[u][t]);
+                df_acc1(ah[t], al[t], pv[u][t], xa[u][t], xb[u][t]);
+                df_norm(xa[u][t], xb[u][t]);
+              }
+              stv<float, CPT>(xh + e, xa[u]);
+              stv<float, CPT>(xl + e, xb[u]);
+            }
+#pragma unroll
+            for (int t = 0; t < CPT; ++t) pv[u][t] = fmaf(bl[t], pv[u][t], fmaf(bh[t], pv[u][t], zv[u][t]));
+          }
+          stv<float, CPT>(pout + e, pv[u]);
+        }
+      }
     }
-    stv<float, CPT>(pout + e, pv);
-  }
-  }
+  };
+  if (step) pass(std::integral_constant<int, 2>{}, true);
+  else pass(std::integral_constant<int, 4>{}, false);
 }
 
 // The x steps still pending after the last iteration K (kl = K): for an
