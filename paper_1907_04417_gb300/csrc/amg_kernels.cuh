@@ -1726,11 +1726,19 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
   // double-float in per-thread shared-memory slots (registers stay free for
   // the gathers); otherwise r is float64 and r.z a float64 register sum
   constexpr int ND = DF ? 1 : CPT, NF = DF ? CPT : 1;
-  __shared__ float sdot[2 * NF][BS];
+  // DF with an even column count: the r.z steps run on column pairs (the
+  // f32x2 forms, each half rounded as its scalar form), slots in sdot2
+  constexpr bool PD = DF && CPT % 2 == 0;
+  constexpr int NQ = PD ? CPT / 2 : 1;
+  __shared__ float sdot[PD ? 1 : 2 * NF][BS];
+  __shared__ F2 sdot2[2 * NQ][PD ? BS : 1];
   double d[ND];
 #pragma unroll
   for (int t = 0; t < ND; ++t) d[t] = 0;
-  if constexpr (DF) {
+  if constexpr (PD) {
+#pragma unroll
+    for (int q = 0; q < 2 * NQ; ++q) sdot2[q][threadIdx.x] = F2{0ull};
+  } else if constexpr (DF) {
 #pragma unroll
     for (int t = 0; t < 2 * NF; ++t) sdot[t][threadIdx.x] = 0.f;
   }
@@ -1790,12 +1798,23 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
 #pragma unroll
         for (int t = 0; t < CPT; ++t) zt[t] = fma(di, fv[t] - acc[t], uv[t]);
         stv<TC, CPT>(z + o, zt);
+        if constexpr (PD) {
 #pragma unroll
-        for (int t = 0; t < CPT; ++t) {
-          float h = sdot[t][threadIdx.x], l = sdot[NF + t][threadIdx.x];
-          df_acc1((float)fv[t], lv[t], (float)zt[t], h, l);
-          sdot[t][threadIdx.x] = h;
-          sdot[NF + t][threadIdx.x] = l;
+          for (int q = 0; q < NQ; ++q) {
+            F2 h = sdot2[q][threadIdx.x], l = sdot2[NQ + q][threadIdx.x];
+            df_acc1_x2(f2_pack((float)fv[2 * q], (float)fv[2 * q + 1]), f2_pack(lv[2 * q], lv[2 * q + 1]),
+                       f2_pack((float)zt[2 * q], (float)zt[2 * q + 1]), h, l);
+            sdot2[q][threadIdx.x] = h;
+            sdot2[NQ + q][threadIdx.x] = l;
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < CPT; ++t) {
+            float h = sdot[t][threadIdx.x], l = sdot[NF + t][threadIdx.x];
+            df_acc1((float)fv[t], lv[t], (float)zt[t], h, l);
+            sdot[t][threadIdx.x] = h;
+            sdot[NF + t][threadIdx.x] = l;
+          }
         }
       }
     } else if (valid && nzl == 0) {
@@ -1825,12 +1844,23 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
   }
   if (mode == 2) return;
   double dd[CPT];
+  if constexpr (PD) {
 #pragma unroll
-  for (int t = 0; t < CPT; ++t) {
-    if constexpr (DF) {
-      dd[t] = (double)sdot[t][threadIdx.x] + (double)sdot[NF + t][threadIdx.x];
-    } else {
-      dd[t] = d[t];
+    for (int q = 0; q < NQ; ++q) {
+      float h0, h1, l0, l1;
+      f2_unpack(sdot2[q][threadIdx.x], h0, h1);
+      f2_unpack(sdot2[NQ + q][threadIdx.x], l0, l1);
+      dd[2 * q] = (double)h0 + (double)l0;
+      dd[2 * q + 1] = (double)h1 + (double)l1;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < CPT; ++t) {
+      if constexpr (DF) {
+        dd[t] = (double)sdot[t][threadIdx.x] + (double)sdot[NF + t][threadIdx.x];
+      } else {
+        dd[t] = d[t];
+      }
     }
   }
   // lanes other than nzl == 0 hold zeros; reduce across the whole warp

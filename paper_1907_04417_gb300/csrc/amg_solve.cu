@@ -463,24 +463,39 @@ __global__ void __launch_bounds__(BS) k_cg_update_df(const int* __restrict__ cta
   }
   // one row range per CTA, or (persistent launch, one system) every
   // gridDim.x-th range
+  // a thread keeps the loads of UN row-column groups in flight before any
+  // arithmetic (the groups in order, so the norm's rounding is unchanged)
+  constexpr int UN = 2;
   for (int chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
   const size_t e0 = (size_t)cta_row[chunk] * K, e1 = (size_t)cta_row[chunk + 1] * K;
-  for (size_t e = e0 + (size_t)threadIdx.x * CPT; e < e1; e += (size_t)BS * CPT) {
-    float ra[CPT], rb[CPT], qa[CPT], qb[CPT], uo[CPT];
-    ldp<float, CPT>(rh + e, ra);
-    ldp<float, CPT>(rl + e, rb);
-    ldv<float, CPT>(qh + e, qa);
-    ldv<float, CPT>(ql + e, qb);
-    float di = u0 ? __ldg(dinv + e / K) : 0.f;
+  for (size_t eb = e0 + (size_t)threadIdx.x * CPT; eb < e1; eb += (size_t)UN * BS * CPT) {
+    float ra[UN][CPT], rb[UN][CPT], qa[UN][CPT], qb[UN][CPT], di[UN];
 #pragma unroll
-    for (int t = 0; t < CPT; ++t) {
-      df_mac(ah[t], al[t], qa[t], qb[t], ra[t], rb[t]);
-      df_acc(ra[t], rb[t], ra[t], rb[t], dh[t], dl[t]);
-      uo[t] = di * ra[t];
+    for (int u = 0; u < UN; ++u) {
+      const size_t e = eb + (size_t)u * BS * CPT;
+      if (e < e1) {
+        ldp<float, CPT>(rh + e, ra[u]);
+        ldp<float, CPT>(rl + e, rb[u]);
+        ldv<float, CPT>(qh + e, qa[u]);
+        ldv<float, CPT>(ql + e, qb[u]);
+        di[u] = u0 ? __ldg(dinv + e / K) : 0.f;
+      }
     }
-    stv<float, CPT>(rh + e, ra);
-    stv<float, CPT>(rl + e, rb);
-    if (u0) stv<float, CPT>(u0 + e, uo);
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+      const size_t e = eb + (size_t)u * BS * CPT;
+      if (e >= e1) continue;
+      float uo[CPT];
+#pragma unroll
+      for (int t = 0; t < CPT; ++t) {
+        df_mac(ah[t], al[t], qa[u][t], qb[u][t], ra[u][t], rb[u][t]);
+        df_acc(ra[u][t], rb[u][t], ra[u][t], rb[u][t], dh[t], dl[t]);
+        uo[t] = di[u] * ra[u][t];
+      }
+      stv<float, CPT>(rh + e, ra[u]);
+      stv<float, CPT>(rl + e, rb[u]);
+      if (u0) stv<float, CPT>(u0 + e, uo);
+    }
   }
   }
   double d[CPT];
