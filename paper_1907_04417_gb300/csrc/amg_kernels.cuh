@@ -1576,8 +1576,23 @@ __global__ void __launch_bounds__(COARSE_BS) k_coarse(int n, int nblk, const int
   const int b0 = __ldg(blk_off + lo), nb = __ldg(blk_off + lo + 1) - b0;
   const double* Ar = inv + __ldg(inv_off + lo) + (size_t)(row - b0) * nb;
   const TC* fc = f + (size_t)b0 * K + c;
+  // even and odd terms in two sums, in order; eight terms' loads requested
+  // before their products
   double s0 = 0.0, s1 = 0.0;
   int j = 0;
+  for (; j + 8 <= nb; j += 8) {
+    double a[8], x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      a[q] = __ldg(Ar + j + q);
+      x[q] = (double)__ldg(fc + (size_t)(j + q) * K);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      s0 = fma(a[q], x[q], s0);
+      s1 = fma(a[q + 1], x[q + 1], s1);
+    }
+  }
   for (; j + 1 < nb; j += 2) {
     s0 = fma(__ldg(Ar + j), (double)__ldg(fc + (size_t)j * K), s0);
     s1 = fma(__ldg(Ar + j + 1), (double)__ldg(fc + (size_t)(j + 1) * K), s1);
