@@ -489,7 +489,7 @@ class Ctx:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps, out
 
-    def kernel_table(self, H, solve, lv, K, mode, names=None):
+    def kernel_table(self, H, solve, lv, K, mode, names=None, workload_key=None):
         """Per kernel family: launches and device time in one solve (events
         around each launch on its stream, in a solve of its own so that the
         timed steps run without them), algorithmic bytes per launch, the
@@ -513,6 +513,9 @@ class Ctx:
             if nb is not None and nl > 0 and ms > 0:
                 gbs = nb / (ms / nl * 1e-3) / 1e9
                 ent.update({"algorithmic_bytes": nb, "achieved_gbs": gbs, "hbm_frac": gbs / self.peak})
+                tr = stored_traffic(name, workload_key) if (workload_key and mode == "df") else None
+                if tr is not None:  # ncu DRAM bytes of the same kernel (profiles/traffic.json)
+                    ent["traffic"] = tr
             tab[name] = ent
         return tab, solve_ms
 
@@ -663,7 +666,7 @@ def run_c2(args, ctx, leg_maker):
           file=sys.stderr, flush=True)
     lv = level_sizes(Hd)
     if not args.no_kernel_table:
-        tab, solve_ms = ctx.kernel_table(Hd, step, lv, args.batch, "df")
+        tab, solve_ms = ctx.kernel_table(Hd, step, lv, args.batch, "df", workload_key=f"aniso{N}_K{args.batch}")
         line["kernels"] = tab
         line["roofline"] = ctx.roofline(tab, lv, args.batch, "df", f"aniso{N}_K{args.batch}")
     # plain float64 solve of one RHS, and of the whole block
