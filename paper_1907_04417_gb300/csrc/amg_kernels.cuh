@@ -299,12 +299,38 @@ template <int NZL>
 __host__ __device__ constexpr int gather_depth() { return NZL == 1 ? 10 : 4; }
 
 // y_i = sum_j a_ij x_j for the K columns owned by this lane.
-template <typename TA, typename TX, int K, int NZL>
+// UB > 0 (one lane group per row): batches of UB; when every row of the
+// warp's pass has exactly UB entries (a warp vote, so all 32 lanes call this)
+// the batch is read without predication, the products in the same order.
+template <typename TA, typename TX, int K, int NZL, int UB = 0>
 __device__ __forceinline__ void row_acc(int i, bool valid, const CsrView<TA>& cv, const TX* __restrict__ x,
                                         int nzl, int cl, TX (&acc)[VT<TX, K>::CPT]) {
-  constexpr int CPT = VT<TX, K>::CPT, CL = VT<TX, K>::CL, U = gather_depth<NZL>();
+  constexpr int CPT = VT<TX, K>::CPT, CL = VT<TX, K>::CL, U = UB > 0 ? UB : gather_depth<NZL>();
 #pragma unroll
   for (int t = 0; t < CPT; ++t) acc[t] = TX(0);
+  if constexpr (UB > 0 && NZL == 1) {
+    int j0 = 0, len = -1;
+    if (valid) {
+      j0 = cv.rp[i - cv.roff];
+      len = cv.rp[i + 1 - cv.roff] - j0;
+    }
+    if (__all_sync(FULL, len == U)) {
+      int c[U];
+      TX a[U], xv[U][CPT];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c[u] = cv.col[j0 + u - cv.coff];
+        a[u] = (TX)cv.val[j0 + u - cv.voff];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) ldv<TX, CPT>(x + (size_t)c[u] * K + cl * CPT, xv[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int t = 0; t < CPT; ++t) acc[t] = fma(a[u], xv[u][t], acc[t]);
+      return;
+    }
+  }
   if (valid) {
     const int j1 = cv.rp[i + 1 - cv.roff];
     int j = cv.rp[i - cv.roff] + nzl;
@@ -1364,6 +1390,13 @@ __global__ void __launch_bounds__(BS, 2) k_group_rs(int ngrp, int zero_e, const 
     extent(pass + 2 * nw, h0, hnb);
     const int g = pass * SPW + slot;
     const int c0 = g < ngrp ? __ldg(ostart + g) : 0, ra = g < ngrp ? __ldg(ostart + g + 1) - c0 : 0;
+    if constexpr (EPI == 1) {
+      // the group's own rows of f and u, read after the batches: into L2 now
+      if (cl == 0 && ra > 0) {
+        prefetch_l2(fo + (size_t)c0 * K, (size_t)ra * K * sizeof(TC));
+        prefetch_l2(x + (size_t)c0 * K, (size_t)ra * K * sizeof(TC));
+      }
+    }
     const int nbw = (int)__reduce_max_sync(FULL, (unsigned)nb);
     TC acc[RS][CPT];
 #pragma unroll
@@ -1722,8 +1755,9 @@ __global__ void __launch_bounds__(BS) k_presmooth0(const int* __restrict__ cta_r
 // Level-0 post-sweep producing the preconditioned residual in float64,
 //   z = u + D^{-1} (f - A u),
 // fused with r.z.  mode 0: rho = r.z (start); mode 1: beta = r.z / rho,
-// rho = r.z; mode 2: no scalars (a bare V-cycle).
-template <typename TC, int K, int NZL, bool DF, bool STG>
+// rho = r.z; mode 2: no scalars (a bare V-cycle).  UQ: the gather batch of
+// row_acc (9 when no row has more entries).
+template <typename TC, int K, int NZL, bool DF, bool STG, int UQ = 0>
 __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, const int* __restrict__ rowptr,
                                               const int* __restrict__ col, const TC* __restrict__ val,
                                               const TC* __restrict__ dinv, const TC* __restrict__ f,
@@ -1805,7 +1839,7 @@ __global__ void __launch_bounds__(BS) k_post0(const int* __restrict__ cta_row, c
       if constexpr (DF) ldv<float, CPT>(rlo + o, lv);
     }
     TC acc[CPT];
-    row_acc<TC, TC, K, NZL>(i, valid, cv, u, nzl, cl, acc);
+    row_acc<TC, TC, K, NZL, UQ>(i, valid, cv, u, nzl, cl, acc);
     if constexpr (DF) {
       if (valid && nzl == 0) {
         TC zt[CPT];

@@ -426,6 +426,11 @@ inline size_t csr_stage_bytes(const Stage& sg) {
         if constexpr (VT<TC, KK>::CL * NZ <= 32) {                                                     \
           auto kern = rlo ? (rp.sg.enabled ? k_post0<TC, KK, NZ, true, true> : k_post0<TC, KK, NZ, true, false>) \
                           : (rp.sg.enabled ? k_post0<TC, KK, NZ, false, true> : k_post0<TC, KK, NZ, false, false>); \
+          if constexpr (NZ == 1) { /* rows of at most 9 entries: batches of 9 */                       \
+            if (L.max_row_len <= 9)                                                                    \
+              kern = rlo ? (rp.sg.enabled ? k_post0<TC, KK, 1, true, true, 9> : k_post0<TC, KK, 1, true, false, 9>) \
+                         : (rp.sg.enabled ? k_post0<TC, KK, 1, false, true, 9> : k_post0<TC, KK, 1, false, false, 9>); \
+          }                                                                                            \
           ensure_smem(kern, smem);                                                                     \
           kern<<<grid > 0 ? grid : rp.ncta, BS, smem, st>>>(rp.cta_row, L.rowptr, L.col, vals<TC>(L), \
                                                             dinvs<TC>(L), f, u, r, rlo, z, ks, mode,   \
